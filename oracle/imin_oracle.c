@@ -1,0 +1,603 @@
+/*
+ * imin_oracle.c -- CPU oracle for the sampled-dominator-tree estimator and the two greedy
+ * drivers of "Minimizing the Influence of Misinformation via Vertex Blocking" (arXiv
+ * 2302.13529).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, plain, obviously-correct statement of what
+ * the GPU path must compute. Only the test suite, the smoke check and the benchmark's CPU
+ * baseline may load it. It shares no code, header or table with the CUDA library; the two
+ * are written independently from the same definitions.
+ *
+ * What it computes, step by step in the paper's order:
+ *   - Random sampled graph g (Def. 4, Sec. 4.2.2): every edge e = (u,v) is kept
+ *     independently with probability p(u,v). Edge e is kept in sample j of call `round`
+ *     iff  W(key, round, j, e) <= thr[e],  where W is one 32-bit word of Philox4x32-10
+ *     (below) and thr = ceil(p * 2^32) - 1 (keep probability (thr+1)/2^32).
+ *   - Multiple seeds are merged into one super-seed s' (Sec. 4, "From Multiple Seeds to One
+ *     Seed"): s' -> s for every seed s. Edges that enter a seed are dropped (a seed is active
+ *     from time 0; the merged graph has no edge into s'). Each original seed edge keeps its
+ *     own draw: the merged edge s' -> u is live iff one of them is, which has exactly the
+ *     probability 1 - prod(1 - p_i) the paper assigns to it.
+ *   - Blockers (Def. 2): every in-edge of a blocked vertex has probability 0, i.e. blocked
+ *     vertices are never reached.
+ *   - Only the part of g reachable from s' matters for dominators from s' (Defs. 5-6 speak
+ *     of paths from s'), so the sample is built by a breadth-first search from the seeds that
+ *     decides each out-edge of a reached vertex exactly once; the recorded live edges among
+ *     reached vertices are the reachable part of g.
+ *   - Dominator tree by Lengauer-Tarjan (Sec. 4.2.3, Lemma 3): DFS numbering from s',
+ *     semidominators with path-compressed EVAL/LINK, implicit idom via Lemma 3, then the
+ *     final fix-up pass in DFS order.
+ *   - c[u] = size of u's dominator subtree (Alg. 2; Thm. 6: c[u] = sigma^{->u}(s', g)).
+ *   - Delta[u] += c[u] for every reached non-seed u (Alg. 2). The paper's division by theta is
+ *     left out: counts are kept as exact uint64 sums, and the argmax is unchanged by the
+ *     common positive factor 1/theta.
+ *   - AdvancedGreedy (Alg. 3) and GreedyReplace (Alg. 4), argmax with strict '>' scanning
+ *     candidates in ascending vertex id (so the smallest id wins ties).
+ *
+ * Philox4x32-10 is written from J. K. Salmon, M. A. Moraes, R. O. Dror, D. E. Shaw,
+ * "Parallel Random Numbers: As Easy as 1, 2, 3", SC'11, Sec. 3.3 (Philox): 4 x 32-bit counter,
+ * 2 x 32-bit key, 10 rounds; each round multiplies counter words 0 and 2 by the two round
+ * multipliers (full 64-bit products), and builds the new counter from the high halves xor'd
+ * with the other two words and the round key, and the low halves; the key is bumped by the
+ * two Weyl constants between rounds.
+ *
+ * Stream layout: for edge id e in sample j of call `round` under 64-bit key K,
+ *   counter = ( (e >> 2) & 0xffffffff, j, round, (e >> 2) >> 32 ),  key = ( K & 0xffffffff, K >> 32 )
+ *   word    = output[e & 3]
+ * so one Philox evaluation serves the four edge ids 4q .. 4q+3.
+ *
+ * `round` numbers the calls of DecreaseESComputation within one query from 0: AdvancedGreedy
+ * uses round i-1 in its i-th iteration; GreedyReplace numbers its phase-1 calls first and
+ * continues the count through phase 2.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_API __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------------------------------
+ * Philox4x32-10
+ * ---------------------------------------------------------------------------------------- */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+ORACLE_API void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* The 32-bit uniform word that decides edge e in sample j of call `round`. */
+ORACLE_API uint32_t oracle_edge_word(uint64_t key, uint32_t round, uint32_t sample, int64_t e)
+{
+    uint64_t q = (uint64_t)e >> 2;
+    uint32_t ctr[4] = {(uint32_t)q, sample, round, (uint32_t)(q >> 32)};
+    uint32_t k[2] = {(uint32_t)key, (uint32_t)(key >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, k, out);
+    return out[e & 3];
+}
+
+/* Def. 4: edge e is present in the sampled graph iff its word is <= its threshold. */
+static int edge_live(uint64_t key, uint32_t round, uint32_t sample, int64_t e, uint32_t thr)
+{
+    return oracle_edge_word(key, round, sample, e) <= thr;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * growable int32 array
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t *a;
+    int64_t n, cap;
+} ivec;
+
+static int iv_push(ivec *v, int32_t x)
+{
+    if (v->n == v->cap) {
+        int64_t nc = v->cap ? v->cap * 2 : 64;
+        int32_t *na = (int32_t *)realloc(v->a, (size_t)nc * sizeof(int32_t));
+        if (!na) return -1;
+        v->a = na;
+        v->cap = nc;
+    }
+    v->a[v->n++] = x;
+    return 0;
+}
+
+static int iv_resize(ivec *v, int64_t n)
+{
+    if (n > v->cap) {
+        int32_t *na = (int32_t *)realloc(v->a, (size_t)n * sizeof(int32_t));
+        if (!na) return -1;
+        v->a = na;
+        v->cap = n;
+    }
+    v->n = n;
+    return 0;
+}
+
+static void iv_free(ivec *v)
+{
+    free(v->a);
+    v->a = NULL;
+    v->n = v->cap = 0;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * graph view and per-query state
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t n;
+    int64_t m;
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const uint32_t *thr;
+} graph_t;
+
+typedef struct {
+    /* size n */
+    int32_t *local;      /* global id -> local id (1..R) in the current sample, 0 if unreached */
+    uint8_t *is_seed;
+    uint8_t *is_blocked;
+    /* per-sample local graph (node 0 = super-seed s') */
+    ivec gid;            /* local -> global (gid[0] = -1) */
+    ivec esrc, edst;     /* live edges among reached vertices, local ids */
+    ivec succ_ptr, succ, pred_ptr, pred;
+    /* Lengauer-Tarjan arrays (local ids) */
+    ivec dfn, vertex, parent, semi, idom, ancestor, label, bucket_head, bucket_next, stack,
+        stack_it, cstack;
+    ivec csize;
+} state_t;
+
+static int state_init(state_t *s, int32_t n)
+{
+    memset(s, 0, sizeof(*s));
+    s->local = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    s->is_seed = (uint8_t *)calloc((size_t)n + 1, 1);
+    s->is_blocked = (uint8_t *)calloc((size_t)n + 1, 1);
+    if (!s->local || !s->is_seed || !s->is_blocked) return -1;
+    return 0;
+}
+
+static void state_free(state_t *s)
+{
+    free(s->local);
+    free(s->is_seed);
+    free(s->is_blocked);
+    ivec *all[] = {&s->gid, &s->esrc, &s->edst, &s->succ_ptr, &s->succ, &s->pred_ptr, &s->pred,
+                   &s->dfn, &s->vertex, &s->parent, &s->semi, &s->idom, &s->ancestor,
+                   &s->label, &s->bucket_head, &s->bucket_next, &s->stack, &s->stack_it,
+                   &s->cstack, &s->csize};
+    for (size_t i = 0; i < sizeof(all) / sizeof(all[0]); i++) iv_free(all[i]);
+}
+
+/* Checks shared by every entry point: CSR shape, vertex ranges, seed uniqueness. */
+static int validate(const graph_t *g, const int32_t *seeds, int32_t ns, const int32_t *blocked,
+                    int32_t nb, state_t *s)
+{
+    if (g->n < 0 || g->m < 0 || !g->row_ptr) return -1;
+    if (g->row_ptr[0] != 0 || g->row_ptr[g->n] != g->m) return -1;
+    for (int32_t u = 0; u < g->n; u++)
+        if (g->row_ptr[u + 1] < g->row_ptr[u]) return -1;
+    for (int64_t e = 0; e < g->m; e++)
+        if (g->col[e] < 0 || g->col[e] >= g->n) return -1;
+    for (int32_t i = 0; i < ns; i++) {
+        if (seeds[i] < 0 || seeds[i] >= g->n || s->is_seed[seeds[i]]) return -1;
+        s->is_seed[seeds[i]] = 1;
+    }
+    for (int32_t i = 0; i < nb; i++) {
+        if (blocked[i] < 0 || blocked[i] >= g->n || s->is_seed[blocked[i]] ||
+            s->is_blocked[blocked[i]])
+            return -1;
+        s->is_blocked[blocked[i]] = 1;
+    }
+    return 0;
+}
+
+/* Build successor and predecessor lists of the local sampled graph (counting sort). */
+static int build_adjacency(state_t *s, int32_t N)
+{
+    int64_t E = s->esrc.n;
+    if (iv_resize(&s->succ_ptr, N + 1) || iv_resize(&s->pred_ptr, N + 1) ||
+        iv_resize(&s->succ, E) || iv_resize(&s->pred, E))
+        return -1;
+    memset(s->succ_ptr.a, 0, (size_t)(N + 1) * sizeof(int32_t));
+    memset(s->pred_ptr.a, 0, (size_t)(N + 1) * sizeof(int32_t));
+    for (int64_t k = 0; k < E; k++) {
+        s->succ_ptr.a[s->esrc.a[k] + 1]++;
+        s->pred_ptr.a[s->edst.a[k] + 1]++;
+    }
+    for (int32_t i = 0; i < N; i++) {
+        s->succ_ptr.a[i + 1] += s->succ_ptr.a[i];
+        s->pred_ptr.a[i + 1] += s->pred_ptr.a[i];
+    }
+    ivec fill_s = {0}, fill_p = {0};
+    if (iv_resize(&fill_s, N) || iv_resize(&fill_p, N)) {
+        iv_free(&fill_s);
+        iv_free(&fill_p);
+        return -1;
+    }
+    memcpy(fill_s.a, s->succ_ptr.a, (size_t)N * sizeof(int32_t));
+    memcpy(fill_p.a, s->pred_ptr.a, (size_t)N * sizeof(int32_t));
+    for (int64_t k = 0; k < E; k++) {
+        s->succ.a[fill_s.a[s->esrc.a[k]]++] = s->edst.a[k];
+        s->pred.a[fill_p.a[s->edst.a[k]]++] = s->esrc.a[k];
+    }
+    iv_free(&fill_s);
+    iv_free(&fill_p);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Lengauer-Tarjan on the local graph with N nodes, root 0. Writes idom (local ids) with
+ * idom[0] = 0, and the DFS preorder in `vertex` (vertex[i] = node with DFS number i).
+ * ---------------------------------------------------------------------------------------- */
+
+/* EVAL's path compression, done with an explicit stack instead of recursion: the nodes on
+ * the ancestor path are compressed from the top down, each taking the smaller-semi label of
+ * its ancestor and then skipping over it. */
+static void lt_compress(state_t *s, int32_t v)
+{
+    int32_t *anc = s->ancestor.a, *lab = s->label.a, *semi = s->semi.a;
+    s->cstack.n = 0;
+    int32_t x = v;
+    while (anc[anc[x]] != -1) {
+        iv_push(&s->cstack, x);
+        x = anc[x];
+    }
+    for (int64_t i = s->cstack.n - 1; i >= 0; i--) {
+        x = s->cstack.a[i];
+        int32_t a = anc[x];
+        if (semi[lab[a]] < semi[lab[x]]) lab[x] = lab[a];
+        anc[x] = anc[a];
+    }
+}
+
+static int32_t lt_eval(state_t *s, int32_t v)
+{
+    if (s->ancestor.a[v] == -1) return v;
+    lt_compress(s, v);
+    return s->label.a[v];
+}
+
+static int lengauer_tarjan(state_t *s, int32_t N)
+{
+    if (iv_resize(&s->dfn, N) || iv_resize(&s->vertex, N) || iv_resize(&s->parent, N) ||
+        iv_resize(&s->semi, N) || iv_resize(&s->idom, N) || iv_resize(&s->ancestor, N) ||
+        iv_resize(&s->label, N) || iv_resize(&s->bucket_head, N) ||
+        iv_resize(&s->bucket_next, N) || iv_resize(&s->stack, N) || iv_resize(&s->stack_it, N))
+        return -1;
+    int32_t *dfn = s->dfn.a, *vertex = s->vertex.a, *parent = s->parent.a, *semi = s->semi.a,
+            *idom = s->idom.a, *anc = s->ancestor.a, *lab = s->label.a, *bh = s->bucket_head.a,
+            *bn = s->bucket_next.a;
+    for (int32_t i = 0; i < N; i++) {
+        dfn[i] = -1;
+        anc[i] = -1;
+        lab[i] = i;
+        bh[i] = -1;
+        idom[i] = -1;
+    }
+    /* Step 1: depth-first search from the root, numbering nodes in preorder. */
+    int32_t cnt = 0, top = 0;
+    int32_t *stk = s->stack.a, *it = s->stack_it.a;
+    dfn[0] = cnt;
+    vertex[cnt++] = 0;
+    parent[0] = -1;
+    stk[top] = 0;
+    it[top] = s->succ_ptr.a[0];
+    top++;
+    while (top > 0) {
+        int32_t v = stk[top - 1];
+        if (it[top - 1] < s->succ_ptr.a[v + 1]) {
+            int32_t w = s->succ.a[it[top - 1]++];
+            if (dfn[w] == -1) {
+                dfn[w] = cnt;
+                vertex[cnt++] = w;
+                parent[w] = v;
+                stk[top] = w;
+                it[top] = s->succ_ptr.a[w];
+                top++;
+            }
+        } else {
+            top--;
+        }
+    }
+    if (cnt != N) return -2; /* every local node is reachable by construction */
+    for (int32_t i = 0; i < N; i++) semi[i] = dfn[i];
+
+    /* Steps 2-3: semidominators in reverse preorder; implicit idoms through buckets. */
+    for (int32_t i = N - 1; i >= 1; i--) {
+        int32_t w = vertex[i];
+        for (int32_t k = s->pred_ptr.a[w]; k < s->pred_ptr.a[w + 1]; k++) {
+            int32_t v = s->pred.a[k];
+            int32_t u = lt_eval(s, v);
+            if (semi[u] < semi[w]) semi[w] = semi[u];
+        }
+        int32_t sd = vertex[semi[w]];
+        bn[w] = bh[sd];
+        bh[sd] = w;
+        int32_t p = parent[w];
+        anc[w] = p; /* LINK(parent(w), w) */
+        for (int32_t v = bh[p]; v != -1; v = bn[v]) {
+            int32_t u = lt_eval(s, v);
+            idom[v] = (semi[u] < semi[v]) ? u : p;
+        }
+        bh[p] = -1;
+    }
+    /* Step 4: explicit idoms in preorder. */
+    for (int32_t i = 1; i < N; i++) {
+        int32_t w = vertex[i];
+        if (idom[w] != vertex[semi[w]]) idom[w] = idom[idom[w]];
+    }
+    idom[0] = 0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * One sampled graph: BFS from the seeds over live edges, dominator tree, subtree sizes.
+ * On return the local graph occupies s->gid (N = s->gid.n nodes incl. the root), s->idom and
+ * s->csize; s->local maps reached global ids to local ids (caller must reset via
+ * clear_sample()).
+ * ---------------------------------------------------------------------------------------- */
+static int run_sample(const graph_t *g, const int32_t *seeds, int32_t ns, uint64_t key,
+                      uint32_t round, uint32_t sample, state_t *s)
+{
+    s->gid.n = 0;
+    s->esrc.n = 0;
+    s->edst.n = 0;
+    if (iv_push(&s->gid, -1)) return -1; /* local 0: super-seed s' */
+    for (int32_t i = 0; i < ns; i++) {
+        int32_t v = seeds[i];
+        s->local[v] = (int32_t)s->gid.n;
+        if (iv_push(&s->gid, v) || iv_push(&s->esrc, 0) || iv_push(&s->edst, s->local[v]))
+            return -1;
+    }
+    /* breadth-first search; the gid array doubles as the queue */
+    for (int64_t qi = 1; qi < s->gid.n; qi++) {
+        int32_t u = s->gid.a[qi];
+        for (int64_t e = g->row_ptr[u]; e < g->row_ptr[u + 1]; e++) {
+            int32_t v = g->col[e];
+            if (s->is_seed[v] || s->is_blocked[v]) continue;
+            if (!edge_live(key, round, sample, e, g->thr[e])) continue;
+            if (s->local[v] == 0) {
+                s->local[v] = (int32_t)s->gid.n;
+                if (iv_push(&s->gid, v)) return -1;
+            }
+            if (iv_push(&s->esrc, (int32_t)qi) || iv_push(&s->edst, s->local[v])) return -1;
+        }
+    }
+    int32_t N = (int32_t)s->gid.n;
+    if (build_adjacency(s, N)) return -1;
+    int rc = lengauer_tarjan(s, N);
+    if (rc) return rc;
+    /* subtree sizes: idom(w) precedes w in DFS preorder, so a reverse preorder sweep adds
+       every finished subtree into its parent */
+    if (iv_resize(&s->csize, N)) return -1;
+    for (int32_t i = 0; i < N; i++) s->csize.a[i] = 1;
+    for (int32_t i = N - 1; i >= 1; i--) {
+        int32_t w = s->vertex.a[i];
+        s->csize.a[s->idom.a[w]] += s->csize.a[w];
+    }
+    return 0;
+}
+
+static void clear_sample(state_t *s)
+{
+    for (int64_t i = 1; i < s->gid.n; i++) s->local[s->gid.a[i]] = 0;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Public entry points (all return 0 on success, negative on invalid input / failure)
+ * ---------------------------------------------------------------------------------------- */
+
+/* Per-sample detail for tests: c_out[v] = subtree size of v (0 if v unreached, seeds
+ * included), idom_out[v] = global id of v's immediate dominator (-1 if the super-seed or v
+ * unreached), *n_reached = |R| including seeds, *n_live = number of live edges among R. */
+ORACLE_API int oracle_sample(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
+                             const uint32_t *thr, const int32_t *seeds, int32_t ns,
+                             const int32_t *blocked, int32_t nb, uint64_t key, uint32_t round,
+                             uint32_t sample, uint32_t *c_out, int32_t *idom_out,
+                             int64_t *n_reached, int64_t *n_live)
+{
+    graph_t g = {n, m, row_ptr, col, thr};
+    state_t s;
+    if (state_init(&s, n)) return -1;
+    int rc = validate(&g, seeds, ns, blocked, nb, &s);
+    if (!rc) rc = run_sample(&g, seeds, ns, key, round, sample, &s);
+    if (!rc) {
+        for (int32_t v = 0; v < n; v++) {
+            c_out[v] = 0;
+            idom_out[v] = -1;
+        }
+        for (int64_t i = 1; i < s.gid.n; i++) {
+            int32_t v = s.gid.a[i];
+            c_out[v] = (uint32_t)s.csize.a[i];
+            idom_out[v] = s.gid.a[s.idom.a[i]];
+        }
+        *n_reached = s.gid.n - 1;
+        *n_live = s.esrc.n - ns;
+    }
+    state_free(&s);
+    return rc;
+}
+
+/* Alg. 2 over samples j in [j0, j1): delta[v] += c[v] for every reached non-seed v.
+ * delta is accumulated into (not cleared). */
+static int decrease_range(const graph_t *g, const int32_t *seeds, int32_t ns, uint64_t key,
+                          uint32_t round, uint32_t j0, uint32_t j1, uint64_t *delta,
+                          state_t *s)
+{
+    for (uint32_t j = j0; j < j1; j++) {
+        int rc = run_sample(g, seeds, ns, key, round, j, s);
+        if (rc) {
+            clear_sample(s);
+            return rc;
+        }
+        for (int64_t i = 1 + ns; i < s->gid.n; i++)
+            delta[s->gid.a[i]] += (uint64_t)s->csize.a[i];
+        clear_sample(s);
+    }
+    return 0;
+}
+
+ORACLE_API int oracle_decrease_range(int32_t n, int64_t m, const int32_t *row_ptr,
+                                     const int32_t *col, const uint32_t *thr,
+                                     const int32_t *seeds, int32_t ns, const int32_t *blocked,
+                                     int32_t nb, uint64_t key, uint32_t round, uint32_t j0,
+                                     uint32_t j1, uint64_t *delta)
+{
+    graph_t g = {n, m, row_ptr, col, thr};
+    state_t s;
+    if (state_init(&s, n)) return -1;
+    int rc = validate(&g, seeds, ns, blocked, nb, &s);
+    if (!rc) {
+        memset(delta, 0, (size_t)n * sizeof(uint64_t));
+        rc = decrease_range(&g, seeds, ns, key, round, j0, j1, delta, &s);
+    }
+    state_free(&s);
+    return rc;
+}
+
+/* Alg. 2 (DecreaseESComputation) on G[V \ B]: delta[v] = sum over theta samples of c[v]. */
+ORACLE_API int oracle_decrease(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
+                               const uint32_t *thr, const int32_t *seeds, int32_t ns,
+                               const int32_t *blocked, int32_t nb, uint32_t theta, uint64_t key,
+                               uint32_t round, uint64_t *delta)
+{
+    return oracle_decrease_range(n, m, row_ptr, col, thr, seeds, ns, blocked, nb, key, round, 0,
+                                 theta, delta);
+}
+
+/* strict-'>' argmax over candidate vertices in ascending id; -1 if there is none */
+static int32_t argmax_mask(const uint64_t *delta, int32_t n, const uint8_t *is_cand)
+{
+    int32_t x = -1;
+    for (int32_t u = 0; u < n; u++)
+        if (is_cand[u] && (x == -1 || delta[u] > delta[x])) x = u;
+    return x;
+}
+
+/* Alg. 3 AdvancedGreedy: b rounds of Alg. 2 on G[V \ B] followed by the argmax over
+ * V \ (S u B). Stops early only when no candidate is left. */
+ORACLE_API int oracle_advanced_greedy(int32_t n, int64_t m, const int32_t *row_ptr,
+                                      const int32_t *col, const uint32_t *thr,
+                                      const int32_t *seeds, int32_t ns, int32_t b,
+                                      uint32_t theta, uint64_t key, int32_t *out_blockers,
+                                      int32_t *out_count)
+{
+    graph_t g = {n, m, row_ptr, col, thr};
+    state_t s;
+    if (b < 0 || theta == 0) return -1;
+    if (state_init(&s, n)) return -1;
+    int rc = validate(&g, seeds, ns, NULL, 0, &s);
+    uint64_t *delta = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
+    uint8_t *cand = (uint8_t *)calloc((size_t)n + 1, 1);
+    if (!delta || !cand) rc = -1;
+    int32_t count = 0;
+    if (!rc) {
+        int32_t left = 0;
+        for (int32_t u = 0; u < n; u++) {
+            cand[u] = !s.is_seed[u];
+            left += cand[u];
+        }
+        for (int32_t i = 0; i < b && left > 0; i++, left--) {
+            memset(delta, 0, (size_t)n * sizeof(uint64_t));
+            rc = decrease_range(&g, seeds, ns, key, (uint32_t)i, 0, theta, delta, &s);
+            if (rc) break;
+            int32_t x = argmax_mask(delta, n, cand);
+            out_blockers[count++] = x;
+            cand[x] = 0;
+            s.is_blocked[x] = 1;
+        }
+    }
+    *out_count = count;
+    free(delta);
+    free(cand);
+    state_free(&s);
+    return rc;
+}
+
+/* Alg. 4 GreedyReplace.
+ * Phase 1: CB = N_out(S) \ S; min(|CB|, b) rounds of Alg. 2 on G[V \ B] with the argmax over
+ *          the remaining CB; the winner leaves CB and is appended to B.
+ * Phase 2: for positions i = |B|-1 down to 0 (reverse insertion order): u = B[i] is unblocked,
+ *          Alg. 2 runs on G[V \ (B \ {u})], the argmax x is taken over V \ (S u B \ {u}) (u
+ *          itself is a candidate again), x takes position i, and the phase stops when x = u.
+ * out_blockers receives B in list order. */
+ORACLE_API int oracle_greedy_replace(int32_t n, int64_t m, const int32_t *row_ptr,
+                                     const int32_t *col, const uint32_t *thr,
+                                     const int32_t *seeds, int32_t ns, int32_t b,
+                                     uint32_t theta, uint64_t key, int32_t *out_blockers,
+                                     int32_t *out_count)
+{
+    graph_t g = {n, m, row_ptr, col, thr};
+    state_t s;
+    if (b < 0 || theta == 0) return -1;
+    if (state_init(&s, n)) return -1;
+    int rc = validate(&g, seeds, ns, NULL, 0, &s);
+    uint64_t *delta = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
+    uint8_t *cand = (uint8_t *)calloc((size_t)n + 1, 1);
+    if (!delta || !cand) rc = -1;
+    int32_t count = 0;
+    uint32_t round = 0;
+    if (!rc) {
+        /* CB: out-neighbours of the seeds that are not seeds themselves */
+        for (int32_t i = 0; i < ns; i++) {
+            int32_t u = seeds[i];
+            for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; e++)
+                if (!s.is_seed[col[e]]) cand[col[e]] = 1;
+        }
+        int32_t ncb = 0;
+        for (int32_t u = 0; u < n; u++) ncb += cand[u];
+        int32_t rounds = ncb < b ? ncb : b;
+        for (int32_t i = 0; i < rounds && !rc; i++) {
+            memset(delta, 0, (size_t)n * sizeof(uint64_t));
+            rc = decrease_range(&g, seeds, ns, key, round++, 0, theta, delta, &s);
+            if (rc) break;
+            int32_t x = argmax_mask(delta, n, cand);
+            cand[x] = 0;
+            out_blockers[count++] = x;
+            s.is_blocked[x] = 1;
+        }
+        /* phase 2: candidates are every vertex that is neither a seed nor blocked */
+        for (int32_t u = 0; u < n; u++) cand[u] = !s.is_seed[u] && !s.is_blocked[u];
+        for (int32_t i = count - 1; i >= 0 && !rc; i--) {
+            int32_t u = out_blockers[i];
+            s.is_blocked[u] = 0;
+            cand[u] = 1;
+            memset(delta, 0, (size_t)n * sizeof(uint64_t));
+            rc = decrease_range(&g, seeds, ns, key, round++, 0, theta, delta, &s);
+            if (rc) break;
+            int32_t x = argmax_mask(delta, n, cand);
+            out_blockers[i] = x;
+            s.is_blocked[x] = 1;
+            cand[x] = 0;
+            if (x == u) break;
+        }
+    }
+    *out_count = count;
+    free(delta);
+    free(cand);
+    state_free(&s);
+    return rc;
+}

@@ -1,0 +1,152 @@
+"""ctypes binding of the C oracle (imin_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the oracle states what the sampled-dominator-tree estimator
+(Alg. 2) and the greedy drivers AdvancedGreedy (Alg. 3) and GreedyReplace (Alg. 4) compute,
+slowly and plainly, on the CPU. Only the tests, the smoke check and the benchmark's CPU
+baseline use it; the product path never imports it.
+
+All functions take numpy arrays; graphs are (n, row_ptr int32[n+1], col int32[m],
+thr uint32[m]).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "imin_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libimin_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+_u64p = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile imin_oracle.c into a shared library next to it (plain C, -O2)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra", "-shared", "-fPIC",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            L.oracle_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+            L.oracle_philox4x32_10.restype = None
+            L.oracle_edge_word.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                           ctypes.c_int64]
+            L.oracle_edge_word.restype = ctypes.c_uint32
+            g = [ctypes.c_int32, ctypes.c_int64, _i32p, _i32p, _u32p]
+            L.oracle_sample.argtypes = g + [_i32p, ctypes.c_int32, _i32p, ctypes.c_int32,
+                                            ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                            _u32p, _i32p, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int64)]
+            L.oracle_decrease_range.argtypes = g + [_i32p, ctypes.c_int32, _i32p, ctypes.c_int32,
+                                                    ctypes.c_uint64, ctypes.c_uint32,
+                                                    ctypes.c_uint32, ctypes.c_uint32, _u64p]
+            L.oracle_decrease.argtypes = g + [_i32p, ctypes.c_int32, _i32p, ctypes.c_int32,
+                                              ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                              _u64p]
+            for name in ("oracle_advanced_greedy", "oracle_greedy_replace"):
+                getattr(L, name).argtypes = g + [_i32p, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_uint32, ctypes.c_uint64, _i32p,
+                                                 ctypes.POINTER(ctypes.c_int32)]
+            for name in ("oracle_sample", "oracle_decrease_range", "oracle_decrease",
+                         "oracle_advanced_greedy", "oracle_greedy_replace"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _g(n, row_ptr, col, thr):
+    return (int(n), int(len(col)), np.ascontiguousarray(row_ptr, dtype=np.int32),
+            np.ascontiguousarray(col, dtype=np.int32), np.ascontiguousarray(thr, dtype=np.uint32))
+
+
+def _ids(a):
+    a = np.ascontiguousarray(np.asarray(a if a is not None else [], dtype=np.int32).reshape(-1))
+    if a.size == 0:
+        a = np.zeros(1, dtype=np.int32)
+        return a, 0
+    return a, int(a.size)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"oracle {what} rejected its input (rc={rc})")
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of a 4-word counter under a 2-word key (SC'11, Sec. 3.3)."""
+    out = np.zeros(4, dtype=np.uint32)
+    lib().oracle_philox4x32_10(np.asarray(ctr, dtype=np.uint32), np.asarray(key, dtype=np.uint32), out)
+    return out
+
+
+def edge_word(key: int, round_: int, sample: int, e: int) -> int:
+    """The uint32 word that decides edge e in sample `sample` of call `round_`."""
+    return int(lib().oracle_edge_word(key, round_, sample, e))
+
+
+def sample(graph, seeds, blocked, key, round_, j):
+    """One sampled graph: returns (c[n] subtree sizes, idom[n] global ids or -1, |R|, #live)."""
+    n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
+    s, ns = _ids(seeds)
+    b, nb = _ids(blocked)
+    c = np.zeros(max(n, 1), dtype=np.uint32)
+    idom = np.zeros(max(n, 1), dtype=np.int32)
+    nr = ctypes.c_int64()
+    nl = ctypes.c_int64()
+    _check(lib().oracle_sample(n, m, rp, col, thr, s, ns, b, nb, key, round_, j, c, idom,
+                               ctypes.byref(nr), ctypes.byref(nl)), "sample")
+    return c[:n], idom[:n], nr.value, nl.value
+
+
+def decrease(graph, seeds, blocked, theta, key, round_=0, j0=0) -> np.ndarray:
+    """Alg. 2 on G[V \\ B]: uint64 Delta[n] = sum of dominator-subtree sizes over samples
+    j0 .. j0+theta-1 (no division by theta)."""
+    n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
+    s, ns = _ids(seeds)
+    b, nb = _ids(blocked)
+    out = np.zeros(max(n, 1), dtype=np.uint64)
+    _check(lib().oracle_decrease_range(n, m, rp, col, thr, s, ns, b, nb, key, round_, j0,
+                                       j0 + theta, out), "decrease")
+    return out[:n]
+
+
+def advanced_greedy(graph, seeds, b, theta, key) -> np.ndarray:
+    """Alg. 3: blockers in selection order."""
+    n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
+    s, ns = _ids(seeds)
+    out = np.zeros(max(b, 1), dtype=np.int32)
+    cnt = ctypes.c_int32()
+    _check(lib().oracle_advanced_greedy(n, m, rp, col, thr, s, ns, b, theta, key, out,
+                                        ctypes.byref(cnt)), "advanced_greedy")
+    return out[:cnt.value].copy()
+
+
+def greedy_replace(graph, seeds, b, theta, key) -> np.ndarray:
+    """Alg. 4: blockers in list order (a replacement keeps its predecessor's position)."""
+    n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
+    s, ns = _ids(seeds)
+    out = np.zeros(max(b, 1), dtype=np.int32)
+    cnt = ctypes.c_int32()
+    _check(lib().oracle_greedy_replace(n, m, rp, col, thr, s, ns, b, theta, key, out,
+                                       ctypes.byref(cnt)), "greedy_replace")
+    return out[:cnt.value].copy()

@@ -1,0 +1,409 @@
+"""Pins for the CPU oracle: every check compares it with something other than itself.
+
+* Philox4x32-10 against published known-answer vectors;
+* the toy graph of Fig. 1 against every value the paper prints for it (Ex. 1, Thm. 2, Ex. 2,
+  Table 3), through exact enumeration and through the oracle's estimator;
+* per-sample subtree sizes and immediate dominators against brute-force vertex deletion;
+* the estimator's expectation against exact FP64/rational enumeration of all worlds (Thm. 4);
+* special cases with closed forms: all-p=1 graphs (the library dominator routine of networkx),
+  out-trees (sum of path-probability products) and the DKS construction of Thm. 1;
+* per-sample invariants and driver properties.
+"""
+from __future__ import annotations
+
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2302_13529_gb300 import workloads as W
+from tests import pins
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------------------------------
+# fixtures
+# ------------------------------------------------------------------------------------------
+
+def load_toy():
+    sec = None
+    edges, spread, dec, greedy = [], [], [], []
+    with open(os.path.join(GOLDEN, "toy_graph.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            if line.startswith("["):
+                sec = line.strip("[]")
+                continue
+            t = line.split()
+            if sec == "edges":
+                edges.append((int(t[0]), int(t[1]), Fraction(t[2])))
+            elif sec == "spread":
+                b = [] if t[0] == "-" else [int(x) for x in t[0].split(",")]
+                spread.append((b, float(t[1])))
+            elif sec == "decrease":
+                dec.append((int(t[0]), float(t[1])))
+            elif sec == "greedy":
+                greedy.append((t[0], int(t[1]), [int(x) for x in t[2].split(",")]))
+    return W.graph_from_edges(9, edges, "toy"), spread, dec, greedy
+
+
+TOY, TOY_SPREAD, TOY_DEC, TOY_GREEDY = load_toy()
+
+
+# ------------------------------------------------------------------------------------------
+# Philox
+# ------------------------------------------------------------------------------------------
+
+def test_philox_known_answers():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([int(x, 16) for x in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        out = O.philox4x32_10(r[0:4], r[4:6])
+        assert [int(x) for x in out] == r[6:10]
+
+
+def test_edge_word_layout():
+    """One Philox call serves edge ids 4q..4q+3: counter (q, sample, round, q>>32)."""
+    key = 0x0123456789ABCDEF
+    for e in (0, 1, 2, 3, 4, 7, 1 << 20, (1 << 34) + 5):
+        q = e >> 2
+        out = O.philox4x32_10([q & 0xFFFFFFFF, 17, 5, q >> 32], [key & 0xFFFFFFFF, key >> 32])
+        assert O.edge_word(key, 5, 17, e) == int(out[e & 3])
+
+
+def test_threshold_encoding_and_live_frequency():
+    """thr = ceil(p 2^32) - 1; the live frequency of r <= thr matches (thr+1)/2^32."""
+    assert W.threshold_of(1) == 0xFFFFFFFF
+    assert W.threshold_of(Fraction(1, 2)) == (1 << 31) - 1
+    assert list(W.TR_THRESHOLDS) == [429496729, 42949672, 4294967]
+    # WC: p = 1/d_in
+    col = np.array([0, 1, 1, 2, 2, 2], dtype=np.int32)
+    thr = W.wc_thresholds(col, 3)
+    assert list(thr) == [0xFFFFFFFF, 0x7FFFFFFF, 0x7FFFFFFF] + [0xFFFFFFFF // 3] * 3
+    for d in (1, 2, 3, 7, 1000):
+        t = 0xFFFFFFFF // d
+        assert t + 1 >= (1 << 32) / d > t  # smallest multiple of 2^-32 that is >= 1/d
+    # binomial check of the word stream against a threshold
+    t = W.threshold_of(Fraction(3, 10))
+    n = 40000
+    hits = sum(O.edge_word(99, 0, j, 5) <= t for j in range(n))
+    p = (t + 1) / 2 ** 32
+    assert abs(hits - n * p) < 5 * math.sqrt(n * p * (1 - p))
+
+
+# ------------------------------------------------------------------------------------------
+# the toy graph: printed values
+# ------------------------------------------------------------------------------------------
+
+def test_toy_exact_spreads_match_paper():
+    for blocked, want in TOY_SPREAD:
+        spread, _, _ = pins.exact_moments(TOY, [0], blocked)
+        assert abs(spread - want) < 1e-6, (blocked, spread, want)
+
+
+def test_toy_exact_decrease_matches_paper():
+    _, dec, _ = pins.exact_moments(TOY, [0])
+    for v, want in TOY_DEC:
+        assert abs(dec[v] - want) < 1e-6, (v, dec[v], want)
+
+
+def test_toy_oracle_estimator_matches_paper():
+    theta = 100_000
+    _, dec, dec2 = pins.exact_moments(TOY, [0])
+    got = O.decrease(TOY, [0], [], theta, key=2024, round_=0).astype(np.float64) / theta
+    for v, want in TOY_DEC:
+        sd = math.sqrt(max(dec2[v] - dec[v] ** 2, 0.0) / theta)
+        assert abs(got[v] - want) <= 6 * sd + 1e-9, (v, got[v], want, sd)
+    assert got[0] == 0  # the seed has no counter
+
+
+def test_toy_greedy_outputs_match_table3():
+    for alg, b, want in TOY_GREEDY:
+        for key in (1, 2, 3):
+            f = O.advanced_greedy if alg == "AG" else O.greedy_replace
+            got = list(f(TOY, [0], b, 20_000, key))
+            if alg == "GR":
+                assert sorted(got) == sorted(want), (alg, b, got)
+            else:
+                assert got == want, (alg, b, got)
+
+
+# ------------------------------------------------------------------------------------------
+# per-sample brute force
+# ------------------------------------------------------------------------------------------
+
+def _small_cases():
+    cases = []
+    for i in range(24):
+        rng = np.random.default_rng(100 + i)
+        n = int(rng.integers(5, 14))
+        m = int(rng.integers(n, 3 * n))
+        g = W.random_small_graph(n, m, seed=200 + i)
+        k = int(rng.integers(1, 4))
+        seeds = rng.choice(n, k, replace=False)
+        rest = [v for v in range(n) if v not in set(seeds)]
+        nb = int(rng.integers(0, 3))
+        blocked = list(rng.choice(rest, min(nb, len(rest)), replace=False))
+        cases.append((g, [int(s) for s in seeds], [int(b) for b in blocked]))
+    return cases
+
+
+@pytest.mark.parametrize("case", range(24))
+def test_sample_matches_vertex_deletion(case):
+    g, seeds, blocked = _small_cases()[case]
+    key = 0xBEEF + case
+    for j in range(12):
+        live = pins.sample_live_edges(g, key, 3, j, O.edge_word)
+        R, c_bf, idom_bf = pins.brute_force_sample(g, seeds, blocked, live)
+        c, idom, nr, _ = O.sample(g, seeds, blocked, key, 3, j)
+        assert nr == len(R)
+        assert (c.astype(np.int64) == c_bf).all(), (case, j, c, c_bf)
+        for v in R:
+            if v not in seeds:
+                assert idom[v] == idom_bf[v], (case, j, v, idom[v], idom_bf[v])
+
+
+def test_decrease_is_sum_of_samples():
+    g, seeds, blocked = _small_cases()[3]
+    theta = 40
+    d = O.decrease(g, seeds, blocked, theta, key=5, round_=2)
+    acc = np.zeros(g.n, dtype=np.int64)
+    for j in range(theta):
+        live = pins.sample_live_edges(g, 5, 2, j, O.edge_word)
+        R, c_bf, _ = pins.brute_force_sample(g, seeds, blocked, live)
+        for u in R:
+            if u not in seeds:
+                acc[u] += c_bf[u]
+    assert (d.astype(np.int64) == acc).all()
+
+
+# ------------------------------------------------------------------------------------------
+# expectation: exact enumeration (Thm. 4)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_estimator_expectation_against_enumeration(seed):
+    rng = np.random.default_rng(seed)
+    n = 8
+    g = W.random_small_graph(n, 14, seed=300 + seed,
+                             p_choices=(Fraction(1, 2), Fraction(1, 4), Fraction(3, 4), 1))
+    n_unc = int((g.thr != 0xFFFFFFFF).sum())
+    if n_unc > 14:
+        pytest.skip("too many uncertain edges")
+    seeds = [int(x) for x in rng.choice(n, 2, replace=False)]
+    _, dec, dec2 = pins.exact_moments(g, seeds)
+    theta = 60_000
+    got = O.decrease(g, seeds, [], theta, key=77 + seed).astype(np.float64) / theta
+    for u in range(n):
+        if u in seeds:
+            assert got[u] == 0
+            continue
+        sd = math.sqrt(max(dec2[u] - dec[u] ** 2, 0.0) / theta)
+        assert abs(got[u] - dec[u]) <= 6 * sd + 1e-9, (u, got[u], dec[u], sd)
+
+
+# ------------------------------------------------------------------------------------------
+# special cases
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(8))
+def test_all_certain_edges_reduce_to_library_dominators(seed):
+    """p = 1 everywhere: every sample is G itself, so Delta/theta equals the dominator-subtree
+    sizes of G from the super-seed, which networkx.immediate_dominators gives."""
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(seed)
+    n = 60
+    g = W.random_small_graph(n, 150, seed=400 + seed, p_choices=(1,))
+    seeds = [int(x) for x in rng.choice(n, 3, replace=False)]
+    G = nx.DiGraph()
+    G.add_node("root")
+    for v in range(n):
+        G.add_node(v)
+    for u in range(n):
+        for e in range(g.row_ptr[u], g.row_ptr[u + 1]):
+            v = int(g.col[e])
+            if v not in seeds:
+                G.add_edge(u, v)
+    for s in seeds:
+        G.add_edge("root", s)
+    idom = nx.immediate_dominators(G, "root")
+    size = {v: 1 for v in idom if v != "root"}
+    # accumulate subtree sizes bottom-up by depth
+    depth = {}
+
+    def dep(v):
+        if v == "root":
+            return 0
+        if v not in depth:
+            depth[v] = dep(idom[v]) + 1
+        return depth[v]
+
+    for v in sorted(size, key=dep, reverse=True):
+        if idom[v] != "root":
+            size[idom[v]] += size[v]
+    theta = 3
+    d = O.decrease(g, seeds, [], theta, key=seed)
+    for v in range(n):
+        want = theta * size.get(v, 0) if v not in seeds else 0
+        assert int(d[v]) == want, (v, int(d[v]), want)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_out_tree_closed_form(seed):
+    """On an out-tree every path is unique, so Delta(u) = sum over v in subtree(u) of the
+    product of edge probabilities on the root->v path (Thm. 4 with unique paths)."""
+    rng = np.random.default_rng(seed)
+    n = 40
+    parent = [-1] + [int(rng.integers(0, v)) for v in range(1, n)]
+    probs = [Fraction(1, 2), Fraction(2, 3), Fraction(9, 10), 1]
+    edges = [(parent[v], v, probs[int(rng.integers(0, 4))]) for v in range(1, n)]
+    g = W.graph_from_edges(n, edges)
+    q = {0: 1.0}
+    pe = {v: float(Fraction(int(W.threshold_of(p)) + 1, 1 << 32)) for (_, v, p) in edges}
+    for v in range(1, n):
+        q[v] = q[parent[v]] * pe[v]
+    want = np.zeros(n)
+    for v in range(1, n):
+        u = v
+        while u != 0:
+            want[u] += q[v]
+            u = parent[u]
+    theta = 50_000
+    got = O.decrease(g, [0], [], theta, key=seed).astype(np.float64) / theta
+    for u in range(1, n):
+        # each sample's c[u] lies in [0, subtree size]; use a Hoeffding-style bound
+        sub = sum(1 for v in range(1, n) if _is_anc(parent, u, v))
+        assert abs(got[u] - want[u]) <= 5 * sub / math.sqrt(theta) / 2 + 1e-9, (u, got[u], want[u])
+
+
+def _is_anc(parent, u, v):
+    while v != -1:
+        if v == u:
+            return True
+        v = parent[v]
+    return False
+
+
+def test_dks_construction():
+    """Thm. 1 construction, all p = 1: blocking A subset of C removes |A| + e(A) vertices,
+    where e(A) counts the source-graph edges with both ends in A."""
+    rng = np.random.default_rng(7)
+    nv = 7
+    src_edges = sorted({tuple(sorted(map(int, rng.choice(nv, 2, replace=False))))
+                        for _ in range(12)})
+    me = len(src_edges)
+    n = 1 + nv + me  # 0 = seed, 1..nv = c_i, nv+1.. = d_j
+    edges = [(0, 1 + i, 1) for i in range(nv)]
+    for j, (x, y) in enumerate(src_edges):
+        edges.append((1 + x, 1 + nv + j, 1))
+        edges.append((1 + y, 1 + nv + j, 1))
+    g = W.graph_from_edges(n, edges)
+    _, _, n_all, _ = O.sample(g, [0], [], 1, 0, 0)
+    assert n_all == n
+    for k in (1, 2, 3):
+        for _ in range(5):
+            A = sorted(int(a) for a in rng.choice(nv, k, replace=False))
+            _, _, n_left, _ = O.sample(g, [0], [1 + a for a in A], 1, 0, 0)
+            eA = sum(1 for (x, y) in src_edges if x in A and y in A)
+            assert n_all - n_left == k + eA
+    # single-vertex decrease: c_i alone cuts no d_j (each has two distinct in-neighbours)
+    d = O.decrease(g, [0], [], 4, key=1)
+    assert all(int(d[1 + i]) == 4 for i in range(nv))
+    assert all(int(d[1 + nv + j]) == 4 for j in range(me))
+
+
+# ------------------------------------------------------------------------------------------
+# invariants on the small Chung-Lu workload
+# ------------------------------------------------------------------------------------------
+
+def test_per_sample_invariants_chung_lu():
+    q = W.tiny_chung_lu_query()
+    g = q.graph
+    seeds = set(int(s) for s in q.seeds)
+    blocked = [int(x) for x in np.setdiff1d(np.arange(20), q.seeds)[:3]]
+    for j in range(40):
+        c, idom, nr, _ = O.sample(g, q.seeds, blocked, q.key, 0, j)
+        reached = np.nonzero(c)[0]
+        nonseed = [v for v in reached if v not in seeds]
+        assert len(reached) == nr
+        assert all(c[b] == 0 for b in blocked)
+        # subtree sizes bounded by |R \ S|
+        assert all(1 <= c[v] <= len(nonseed) for v in nonseed)
+        # subtrees hanging off the super-seed or a seed partition R \ S
+        tops = [v for v in nonseed if idom[v] == -1 or idom[v] in seeds]
+        assert sum(int(c[v]) for v in tops) == len(nonseed)
+        # sum of subtree sizes = sum of depths below the seeds
+        def depth(v):
+            d = 0
+            while v != -1 and v not in seeds:
+                d += 1
+                v = idom[v]
+            return d
+        assert sum(int(c[v]) for v in nonseed) == sum(depth(v) for v in nonseed)
+
+
+def test_decrease_zero_on_seeds_and_blocked():
+    q = W.tiny_chung_lu_query()
+    blocked = [int(x) for x in np.setdiff1d(np.arange(40), q.seeds)[:5]]
+    d = O.decrease(q.graph, q.seeds, blocked, 300, q.key)
+    assert all(d[int(s)] == 0 for s in q.seeds)
+    assert all(d[b] == 0 for b in blocked)
+
+
+# ------------------------------------------------------------------------------------------
+# drivers
+# ------------------------------------------------------------------------------------------
+
+def test_advanced_greedy_trace():
+    """Alg. 3: the i-th blocker is the strict argmax (smallest id on ties) of the i-th call of
+    Alg. 2 on G[V \\ B_prefix] over V \\ (S u B_prefix)."""
+    q = W.tiny_chung_lu_query()
+    theta, b = 2000, 5
+    B = O.advanced_greedy(q.graph, q.seeds, b, theta, q.key)
+    assert len(B) == b and len(set(B)) == b
+    for i in range(b):
+        d = O.decrease(q.graph, q.seeds, B[:i], theta, q.key, round_=i).astype(np.int64)
+        d[q.seeds] = -1
+        d[B[:i]] = -1
+        assert int(np.argmax(d)) == B[i]  # numpy argmax returns the first maximum
+
+
+def test_greedy_replace_blocks_all_out_neighbours_when_budget_allows():
+    """If |N_out(S) \\ S| <= b, GR blocks exactly N_out(S) \\ S and the spread is |S|."""
+    rng = np.random.default_rng(3)
+    n = 30
+    g = W.random_small_graph(n, 70, seed=9, p_choices=(Fraction(3, 4), 1))
+    seeds = [0, 1]
+    nout = set()
+    for s in seeds:
+        nout |= {int(v) for v in g.col[g.row_ptr[s]:g.row_ptr[s + 1]]}
+    nout -= set(seeds)
+    B = O.greedy_replace(g, seeds, len(nout) + 2, 4000, key=11)
+    assert set(int(x) for x in B) == nout
+    _, _, nr, _ = O.sample(g, seeds, list(B), 11, 0, 0)
+    assert nr == len(seeds)
+
+
+def test_greedy_edge_cases():
+    g = W.graph_from_edges(4, [(0, 1, 1), (1, 2, 1)])
+    # seed with no out-neighbours outside S: GR returns nothing
+    assert len(O.greedy_replace(g, [2], 3, 10, 1)) == 0
+    # AG stops when V \ (S u B) is exhausted
+    assert sorted(O.advanced_greedy(g, [0], 10, 10, 1)) == [1, 2, 3]
+    # b = 0
+    assert len(O.advanced_greedy(g, [0], 0, 10, 1)) == 0
+    with pytest.raises(ValueError):
+        O.decrease(g, [0, 0], [], 10, 1)  # duplicate seed
+    with pytest.raises(ValueError):
+        O.decrease(g, [0], [0], 10, 1)  # blocked seed
