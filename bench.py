@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 sampled-dominator-tree estimator.
+
+A step is one AdvancedGreedy query (Alg. 3): b rounds, each one Alg. 2 call over theta sampled
+graphs (live-edge decisions, BFS from the seeds, dominator tree, subtree sizes, counter
+update) followed by the blocker selection. Workload: R-MAT n=2^17, m=2^20 (a,b,c,d =
+.57/.19/.19/.05), weighted-cascade thresholds, |S|=50 uniform seeds, b=50, theta=10^5.
+
+value = sampled graphs processed per second (b * theta per step) with the graph and the seed
+set already on the device; e2e = the same metric through the C ABI from pinned host buffers,
+graph upload and blocker read-back included in every step.
+
+Under torchrun (N > 1) every rank runs an independent query replica on its own GPU (the path
+has no exchange step); value = samples of all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "samples/s batched vs one-query-per-launch (bit-exact); AG/GR wall time; p99"
+WORKLOAD = "rmat17-wc-advanced-greedy"
+L2_FLUSH_BYTES = 512 << 20
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="target CPU time of the oracle baseline sample")
+    return p.parse_args(argv)
+
+
+# --------------------------------------------------------------------------------------------
+# ranks and aggregation
+# --------------------------------------------------------------------------------------------
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def aggregate(local_seconds: float, local_units: float, world: int, reduce_max=None,
+              reduce_sum=None):
+    """Whole-job throughput: units of all ranks / slowest rank's time (max over ranks)."""
+    t = reduce_max(local_seconds) if reduce_max else local_seconds
+    u = reduce_sum(local_units) if reduce_sum else local_units * world
+    return u / t if t > 0 else 0.0, t
+
+
+def make_reducers(dist):
+    if dist is None:
+        return None, None
+    import torch
+
+    def red(x, op):
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    return (lambda x: red(x, dist.ReduceOp.MAX)), (lambda x: red(x, dist.ReduceOp.SUM))
+
+
+# --------------------------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="imin_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.path is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(REASONS, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------------------------
+# roofline accounting
+# --------------------------------------------------------------------------------------------
+
+def algorithmic_bytes(stats: dict, tier: int, n_seeds: int) -> float:
+    """Bytes the method must move for the samples finished by one kernel tier:
+    8|R| (row offsets of every reached vertex) + 4 E_R (threshold of every examined edge)
+    + 4 L (target of every live edge) + 8 |R \\ S| (one uint64 counter per reached non-seed)."""
+    r = stats["tier_reached"][tier]
+    e = stats["tier_examined_edges"][tier]
+    l_ = stats["tier_live_edges"][tier]
+    s = stats["tier_samples"][tier] * n_seeds
+    return 8.0 * r + 4.0 * e + 4.0 * l_ + 8.0 * (r - s)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2302_13529_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
+    current kernel sources (profiles/<kernel>_<workload>.md: 'source_hash:' and
+    'dram_bytes_per_launch:' lines); None otherwise."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{WORKLOAD}.md")
+    if not os.path.exists(path):
+        return None
+    src, val = None, None
+    for line in open(path):
+        if line.startswith("source_hash:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            val = float(line.split(":", 1)[1].strip())
+    return val if src == kernel_source_hash() else None
+
+
+# --------------------------------------------------------------------------------------------
+# arms
+# --------------------------------------------------------------------------------------------
+
+def cpu_baseline(q, seconds: float):
+    """The oracle as it stands (single-threaded C), on a bounded sample of the workload:
+    the first `count` sampled graphs of round 0, sized to take about `seconds`."""
+    from oracle import oracle as O
+
+    O.lib()
+    t = time.perf_counter()
+    O.decrease(q.graph, q.seeds, [], 200, q.key, 0)
+    per = (time.perf_counter() - t) / 200
+    count = int(max(200, min(q.theta, seconds / max(per, 1e-7))))
+    t = time.perf_counter()
+    O.decrease(q.graph, q.seeds, [], count, q.key, 0)
+    dt = time.perf_counter() - t
+    return {"value": count / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"round 0, samples 0..{count - 1} of theta={q.theta} ({dt:.1f} s)"}
+
+
+def run_reference(args, q, rank):
+    """The oracle timed on the host cores on the same workload, metric and unit; each step is a
+    bounded sample (a range of sampled graphs of one round)."""
+    from oracle import oracle as O
+
+    if rank != 0:
+        return
+    O.lib()
+    t = time.perf_counter()
+    O.decrease(q.graph, q.seeds, [], 100, q.key, 0)
+    per = (time.perf_counter() - t) / 100
+    per_step = int(max(100, min(q.theta, 10.0 / max(per, 1e-7))))
+    for w in range(args.warmup):
+        O.decrease(q.graph, q.seeds, [], min(per_step, 200), q.key, w)
+    times = []
+    for k in range(args.steps):
+        t = time.perf_counter()
+        O.decrease(q.graph, q.seeds, [], per_step, q.key, k, (k * per_step) % q.theta)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "uint32", "data": "synthetic",
+            "config": config_of(q),
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} sampled graphs of one round per step"},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(q):
+    return {"workload": WORKLOAD, "graph": "R-MAT scale 17, m=2^20, (0.57,0.19,0.19,0.05), WC",
+            "n": q.graph.n, "m": q.graph.m, "seeds": int(len(q.seeds)), "b": q.b,
+            "theta": q.theta, "samples_per_step": q.b * q.theta,
+            "l2": "flushed between steps (512 MiB write outside the step events)"}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local_rank = dist_env()
+    from paper_2302_13529_gb300 import workloads as W
+
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        import torch
+        if args.impl == "ours" and torch.cuda.is_available():
+            torch.cuda.set_device(local_rank)
+            tdist.init_process_group("nccl")
+        else:
+            tdist.init_process_group("gloo")
+        dist = tdist
+
+    q = W.rmat17_query()
+    if args.impl == "reference":
+        run_reference(args, q, rank)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+    from paper_2302_13529_gb300 import build, imin
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    key = q.key + rank  # independent replica per rank
+    gh = imin.load_graph(q.graph)
+    seeds_d = torch.from_numpy(q.seeds).to(dev)
+    out_d = torch.empty(q.b, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        imin.advanced_greedy(gh, seeds_d, q.b, q.theta, key, out=out_d)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    reduce_max, reduce_sum = make_reducers(dist)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    imin.profile_read(reset=True)
+    imin.profile_enable(True)
+    stats_sum = None
+    launches0 = imin.launch_count()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0])
+                      if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit()
+                      else local_rank) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            step()
+            stops[k].record(stream)
+            st = imin.last_stats()
+            if stats_sum is None:
+                stats_sum = st
+            else:
+                for kk, vv in st.items():
+                    stats_sum[kk] = ([a + b for a, b in zip(stats_sum[kk], vv)]
+                                     if isinstance(vv, list) else stats_sum[kk] + vv)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = imin.launch_count() - launches0
+    imin.profile_enable(False)
+    prof = imin.profile_read(reset=True)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, stops)]
+    local_s = sum(step_ms) / 1e3
+    samples_local = q.b * q.theta * args.steps
+    value, slowest = aggregate(local_s, samples_local, world, reduce_max, reduce_sum)
+    ms_per_step = 1e3 * slowest / args.steps
+
+    # roofline of the dominant kernel (the sample tier with the most device time)
+    tiers = [("sample_tier0", 0), ("sample_tier1", 1), ("sample_tier2", 2)]
+    kname, tier = max(tiers, key=lambda kt: prof[kt[0]]["ms"])
+    kp = prof[kname]
+    avg_ms = kp["ms"] / max(kp["launches"], 1)
+    alg_bytes = algorithmic_bytes(stats_sum, tier, len(q.seeds)) / max(kp["launches"], 1)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(f"k_sample_tier{tier}")
+    total_ms = sum(v["ms"] for v in prof.values())
+    roofline = {"kernel": f"k_sample_tier<{tier}>", "bound": "hbm", "achieved": achieved,
+                "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": avg_ms, "share_of_device_time": kp["ms"] / max(total_ms, 1e-9),
+                "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
+
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "uint32",
+            "data": "synthetic", "config": config_of(q), "roofline": roofline,
+            "gpu_launches": launches,
+            "work": {"reached_per_sample": stats_sum["reached"] / stats_sum["samples"],
+                     "examined_edges_per_sample": stats_sum["examined_edges"] / stats_sum["samples"],
+                     "live_edges_per_sample": stats_sum["live_edges"] / stats_sum["samples"],
+                     "live_edges_per_s": value * stats_sum["live_edges"] / stats_sum["samples"],
+                     "tier_samples": stats_sum["tier_samples"]},
+            "ag_wall_s": ms_per_step / 1e3}
+    clocks = clk.summary()
+    if clocks is not None:
+        line["clocks"] = clocks
+
+    # GreedyReplace wall time (one query, device-resident inputs)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    imin.greedy_replace(gh, seeds_d, q.b, q.theta, key, out=out_d)
+    torch.cuda.synchronize()
+    line["gr_wall_s"] = time.perf_counter() - t
+
+    # end to end through the C ABI from pinned host buffers
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        rp_h, col_h, thr_h = pin(q.graph.row_ptr), pin(q.graph.col), pin(q.graph.thr.view(np.int32))
+        seeds_h = pin(q.seeds)
+        out_h = torch.empty(q.b, dtype=torch.int32).pin_memory()
+        h2d = rp_h.numel() * 4 + col_h.numel() * 4 + thr_h.numel() * 4 + seeds_h.numel() * 4
+        d2h = out_h.numel() * 4
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(e2e_steps):
+            g2 = imin.GraphHandle(q.graph.n, rp_h, col_h, thr_h.view(torch.uint32))
+            imin.advanced_greedy(g2, seeds_h, q.b, q.theta, key, out=out_h)
+            g2.close()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t
+        e2e_value, _ = aggregate(e2e_s, q.b * q.theta * e2e_steps, world, reduce_max, reduce_sum)
+        line["e2e"] = {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                       "includes": "graph upload + validation, seed upload, 50 rounds, "
+                                   "blocker read-back"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(q, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * imin.h -- C ABI of the GB300 library for influence minimization by vertex blocking
+ * (arXiv 2302.13529): the sampled-dominator-tree estimator (Alg. 2) and the greedy drivers
+ * AdvancedGreedy (Alg. 3) and GreedyReplace (Alg. 4), computed by sm_103a CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: IMIN_OK (0) on success, a negative IMIN_ERR_* code otherwise. On failure
+ *     imin_last_error() returns a message for the calling thread. No exception crosses the ABI.
+ *   - Pointers: every array argument may be host memory or device memory of the current CUDA
+ *     device; the library detects which (cudaPointerGetAttributes). The caller owns and frees
+ *     its arrays; the library copies what it keeps.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream). Work is enqueued on
+ *     it. Calls that return host-visible results (host output buffers, counts) synchronize the
+ *     stream before returning; calls whose outputs are all device buffers may return before
+ *     the kernels finish.
+ *   - Graph: directed, CSR by source. Vertex ids are 0..n-1; edge e of vertex u lies in
+ *     [row_ptr[u], row_ptr[u+1]). Each edge carries a uint32 threshold thr[e] that encodes its
+ *     independent-cascade probability p(u,v) (Sec. 3.1) as thr = ceil(p * 2^32) - 1: edge e is
+ *     live in a sample when the sample's 32-bit uniform word for e is <= thr[e], so it is live
+ *     with probability (thr+1)/2^32; thr = 0xFFFFFFFF means p = 1. Edges with p = 0 must be
+ *     left out. Multi-edges and self-loops are accepted (self-loops never matter).
+ *   - Random stream (Def. 4 sampled graphs): the word for edge e in sample j of call `round`
+ *     under the 64-bit key K is word (e & 3) of Philox4x32-10 (Salmon et al., SC'11) with
+ *     counter (e >> 2, j, round, 0) and key (K mod 2^32, K >> 32). Results therefore depend
+ *     only on (graph, seed set, blocked set, theta, key, round) -- never on launch shape,
+ *     stream, batching or device.
+ *   - Seeds (Sec. 4, multiple seeds merged into one super-seed): seeds must be distinct; edges
+ *     into seeds are ignored; seeds have no counter and are never chosen as blockers.
+ *   - Blockers (Def. 2): every in-edge of a blocked vertex has probability 0.
+ *   - Counters: the decrease counter of vertex u is the exact integer sum over the theta
+ *     samples of the size of u's dominator subtree (Alg. 2 without its division by theta;
+ *     Thm. 6). Dividing by theta gives the paper's estimate of the expected-spread decrease.
+ */
+#ifndef IMIN_H
+#define IMIN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IMIN_OK 0
+#define IMIN_ERR_INVALID (-1)   /* an argument violates the contract above */
+#define IMIN_ERR_CUDA (-2)      /* a CUDA runtime call failed */
+#define IMIN_ERR_NOMEM (-3)     /* device memory could not be allocated */
+#define IMIN_ERR_CAPACITY (-4)  /* a sampled cascade exceeded the largest kernel tier */
+#define IMIN_ERR_INTERNAL (-5)  /* a kernel reported an internal consistency failure */
+
+/* Opaque handle: a directed graph resident in device memory. */
+typedef struct imin_graph imin_graph;
+
+/* Load a graph (Sec. 3: G = (V, E) with probabilities p(u,v)) into device memory.
+ *   n        number of vertices, 0 < n < 2^31
+ *   m        number of edges, 0 <= m < 2^31; m == row_ptr[n]
+ *   row_ptr  int32[n+1], non-decreasing, row_ptr[0] == 0
+ *   col      int32[m], targets in [0, n)
+ *   thr      uint32[m], thresholds as described above
+ *   stream   stream for the uploads (synchronized before return)
+ *   out      receives the handle; free it with imin_free_graph
+ * Errors: IMIN_ERR_INVALID for a malformed CSR, IMIN_ERR_NOMEM, IMIN_ERR_CUDA. */
+int imin_load_graph(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t* col,
+                    const uint32_t* thr, void* stream, imin_graph** out);
+
+/* Release a graph handle and its device memory (after all work using it has finished).
+ * NULL is accepted. */
+int imin_free_graph(imin_graph* g);
+
+/* Number of vertices and edges of a loaded graph (either pointer may be NULL). */
+int imin_graph_info(const imin_graph* g, int32_t* n, int64_t* m);
+
+/* DecreaseESComputation (Alg. 2) on G[V \ B].
+ *   seeds, n_seeds      S: int32[n_seeds], distinct, 1 <= n_seeds <= n
+ *   blocked, n_blocked  B: int32[n_blocked], distinct, disjoint from S (NULL if n_blocked == 0)
+ *   theta               number of sampled graphs, >= 1
+ *   key, round          select the random stream (see above); `round` is the 0-based index of
+ *                       this call within a greedy run
+ *   out_delta           uint64[n]: out_delta[u] = sum over the theta samples of the size of u's
+ *                       subtree in the sample's dominator tree rooted at the super-seed
+ *                       (Thm. 6: the number of reached vertices whose every path from S passes
+ *                       through u); 0 for seeds, blocked and unreached vertices.
+ * Errors: IMIN_ERR_INVALID, IMIN_ERR_NOMEM, IMIN_ERR_CUDA, IMIN_ERR_CAPACITY. */
+int imin_estimate_decrease(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
+                           const int32_t* blocked, int32_t n_blocked, uint32_t theta,
+                           uint64_t key, uint32_t round, uint64_t* out_delta, void* stream);
+
+/* AdvancedGreedy (Alg. 3): b rounds; round i (0-based) runs Alg. 2 with round index i on
+ * G[V \ B] and appends the candidate of V \ (S u B) with the largest counter (strict '>' in
+ * ascending vertex id, so the smallest id wins ties). Stops early only when V \ (S u B) is
+ * empty.
+ *   b             budget, >= 0
+ *   out_blockers  int32[b]: the blockers in selection order
+ *   out_count     host int32: number of blockers written (min(b, n - n_seeds))
+ * Synchronizes `stream`. Errors as for imin_estimate_decrease. */
+int imin_advanced_greedy(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
+                         int32_t b, uint32_t theta, uint64_t key, int32_t* out_blockers,
+                         int32_t* out_count, void* stream);
+
+/* GreedyReplace (Alg. 4).
+ *   Phase 1: CB = out-neighbours of S that are not seeds; k = min(|CB|, b) rounds (round
+ *            indices 0..k-1) each run Alg. 2 on G[V \ B] and move the best remaining CB vertex
+ *            into B (appended).
+ *   Phase 2: for positions i = k-1 down to 0 (reverse insertion order), with round indices
+ *            continuing from k: u = B[i] is unblocked, Alg. 2 runs on G[V \ (B \ {u})], the
+ *            best vertex x of V \ (S u B \ {u}) (u included) takes position i, and the phase
+ *            ends as soon as x == u.
+ *   out_blockers  int32[b]: B in list order; out_count: k.
+ * Synchronizes `stream`. Errors as for imin_estimate_decrease. */
+int imin_greedy_replace(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b,
+                        uint32_t theta, uint64_t key, int32_t* out_blockers, int32_t* out_count,
+                        void* stream);
+
+/* Work counters of one Alg. 2 call, for throughput accounting (not part of the method). */
+typedef struct imin_stats {
+    uint64_t samples;        /* sampled graphs processed (theta) */
+    uint64_t reached;        /* sum over samples of |R|, seeds included */
+    uint64_t examined_edges; /* sum over samples of the out-edges of reached vertices */
+    uint64_t live_edges;     /* sum over samples of live edges into reached non-seed vertices */
+    uint64_t nontree_edges;  /* live edges that were not BFS discovery edges */
+    uint64_t dom_passes;     /* dominator fixed-point passes */
+    /* per kernel tier (0: shared-memory working set, 1: per-warp global scratch for up to 16K
+       reached vertices, 2: whole-graph scratch), counting the samples each tier finished */
+    uint64_t tier_samples[3];
+    uint64_t tier_reached[3];
+    uint64_t tier_examined_edges[3];
+    uint64_t tier_live_edges[3];
+} imin_stats;
+
+/* imin_estimate_decrease plus the work counters of the call. Synchronizes `stream`. */
+int imin_estimate_decrease_stats(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
+                                 const int32_t* blocked, int32_t n_blocked, uint32_t theta,
+                                 uint64_t key, uint32_t round, uint64_t* out_delta,
+                                 imin_stats* stats, void* stream);
+
+/* ---- measurement hooks (throughput accounting; the paper has no counterpart) ------------- */
+
+/* Work counters of the last successful estimate / greedy call on the calling thread, summed
+ * over all of that call's Alg. 2 rounds. */
+int imin_last_stats(imin_stats* out);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+uint64_t imin_launch_count(void);
+
+/* Per-kind kernel timing. When enabled, every kernel launch of the entry points above is
+ * bracketed by CUDA events recorded on the stream it is launched on; the elapsed times are
+ * added up when the entry point synchronizes. Kinds: 0-2 = sample tiers 0-2, 3 = blocker
+ * selection, 4 = other small kernels (only launches of kind 4 made by the greedy drivers are
+ * timed). Timing adds event records between launches; leave it off when measuring
+ * whole-call throughput. */
+typedef struct imin_profile {
+    uint64_t launches[5];
+    double ms[5];
+} imin_profile;
+int imin_profile_enable(int on);
+int imin_profile_read(imin_profile* out, int reset);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* imin_last_error(void);
+
+/* ABI version of this header (IMIN_ABI_VERSION). */
+#define IMIN_ABI_VERSION 1
+int imin_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IMIN_H */

@@ -1,0 +1,643 @@
+// api.cu -- the C ABI declared in include/imin.h.
+//
+// Host code only: argument checks, device buffers, and the order of kernel launches that
+// makes up Alg. 2 (one call), Alg. 3 (b calls, each followed by a selection) and Alg. 4
+// (phase-1 calls with selection over CB, then replacement calls with an on-device stop flag).
+// All launches of one entry point go to the caller's stream; per-call buffers come from the
+// stream-ordered allocator and are released on the same stream.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "imin.h"
+#include "internal.h"
+
+using namespace imin;
+
+struct imin_graph {
+    int32_t n = 0;
+    int32_t m = 0;
+    int device = 0;
+    DeviceInfo dev;
+    int32_t* row_ptr = nullptr;
+    int32_t* col = nullptr;
+    uint4* thr4 = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int fail_cuda(cudaError_t e, const char* where)
+{
+    cudaGetLastError();  // clear a sticky launch error, if any
+    const int code = e == cudaErrorMemoryAllocation ? IMIN_ERR_NOMEM : IMIN_ERR_CUDA;
+    return fail(code, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define IMIN_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return fail_cuda(e_, #call); \
+    } while (0)
+
+// ---- measurement hooks (not part of the method) -------------------------------------------
+// Kernel kinds: the three sample tiers, the selection, everything else.
+enum Kind { kKindTier0 = 0, kKindTier1, kKindTier2, kKindSelect, kKindOther, kKinds };
+
+std::atomic<uint64_t> g_launches{0};
+std::atomic<int> g_profile_on{0};
+std::mutex g_prof_mu;
+uint64_t g_prof_launches[kKinds] = {};
+double g_prof_ms[kKinds] = {};
+thread_local imin_stats g_last_stats = {};
+
+// CUDA-event timing of each launch of one entry point, on the stream it is launched on.
+struct CallTimer {
+    cudaStream_t s;
+    bool on;
+    std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> recs;
+    explicit CallTimer(cudaStream_t st) : s(st), on(g_profile_on.load() != 0) {}
+    ~CallTimer()
+    {
+        for (auto& r : recs) {
+            cudaEventDestroy(std::get<1>(r));
+            cudaEventDestroy(std::get<2>(r));
+        }
+    }
+    // Enqueue `launch` (returns cudaError_t, sets *launched) bracketed by events.
+    template <typename F>
+    cudaError_t run(int kind, F&& launch)
+    {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (on) {
+            cudaError_t e = cudaEventCreate(&a);
+            if (e == cudaSuccess) e = cudaEventCreate(&b);
+            if (e == cudaSuccess) e = cudaEventRecord(a, s);
+            if (e != cudaSuccess) return e;
+        }
+        bool launched = false;
+        cudaError_t e = launch(&launched);
+        if (launched) g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (on) {
+            if (e == cudaSuccess && launched) e = cudaEventRecord(b, s);
+            recs.emplace_back(launched ? kind : -1, a, b);
+        }
+        return e;
+    }
+    // After the stream has been synchronized: add the measured times to the totals.
+    void collect()
+    {
+        if (!on) return;
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        for (auto& r : recs) {
+            const int kind = std::get<0>(r);
+            if (kind < 0) continue;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, std::get<1>(r), std::get<2>(r)) == cudaSuccess) {
+                g_prof_ms[kind] += ms;
+                g_prof_launches[kind] += 1;
+            }
+        }
+    }
+};
+
+bool is_device_ptr(const void* p)
+{
+    if (p == nullptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy `count` elements that may live on the host or the device into a host vector.
+template <typename T>
+int to_host(const T* p, int64_t count, std::vector<T>& out, cudaStream_t s, const char* what)
+{
+    out.resize(static_cast<size_t>(count));
+    if (count == 0) return IMIN_OK;
+    if (p == nullptr) return fail(IMIN_ERR_INVALID, std::string(what) + " is NULL");
+    if (is_device_ptr(p)) {
+        IMIN_CUDA(cudaMemcpyAsync(out.data(), p, sizeof(T) * count, cudaMemcpyDeviceToHost, s));
+        IMIN_CUDA(cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(out.data(), p, sizeof(T) * count);
+    }
+    return IMIN_OK;
+}
+
+// Stream-ordered device buffers released at scope exit.
+struct Arena {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Arena(cudaStream_t st) : s(st) {}
+    ~Arena()
+    {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    cudaError_t alloc(T** out, uint64_t count)
+    {
+        void* p = nullptr;
+        const uint64_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e == cudaSuccess) ptrs.push_back(p);
+        *out = static_cast<T*>(p);
+        return e;
+    }
+};
+
+void keep_pool_memory(int device)
+{
+    static bool done[64] = {};
+    if (device < 0 || device >= 64 || done[device]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t threshold = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+    }
+    done[device] = true;
+}
+
+int check_ids(const std::vector<int32_t>& ids, int32_t n, std::vector<uint8_t>& mark, uint8_t tag,
+              const char* what)
+{
+    for (int32_t v : ids) {
+        if (v < 0 || v >= n) return fail(IMIN_ERR_INVALID, std::string(what) + ": vertex id out of range");
+        if (mark[v] != 0) {
+            return fail(IMIN_ERR_INVALID, std::string(what) +
+                        (mark[v] == tag ? ": duplicate vertex" : ": vertex is also a seed"));
+        }
+        mark[v] = tag;
+    }
+    return IMIN_OK;
+}
+
+DevGraph dev_graph(const imin_graph* g)
+{
+    return DevGraph{g->n, g->m, g->row_ptr, g->col, g->thr4};
+}
+
+// Everything one query needs on the device besides its graph.
+struct Query {
+    Arena arena;
+    TierPlan plan{};
+    int32_t* seeds = nullptr;
+    uint32_t* excl = nullptr;
+    unsigned long long* delta = nullptr;
+    uint32_t* lists = nullptr;
+    unsigned long long* stats = nullptr;
+    uint8_t* scratch1 = nullptr;
+    uint8_t* scratch2 = nullptr;
+    int32_t words = 0;
+    explicit Query(cudaStream_t s) : arena(s) {}
+};
+
+int setup_query(const imin_graph* g, const std::vector<int32_t>& seeds, uint32_t theta,
+                unsigned long long* out_delta_dev, Query& q)
+{
+    cudaStream_t s = q.arena.s;
+    q.words = (g->n + 31) / 32;
+    q.plan = plan_tiers(g->dev, g->n, g->m, static_cast<uint32_t>(seeds.size()));
+    IMIN_CUDA(q.arena.alloc(&q.seeds, seeds.size()));
+    IMIN_CUDA(q.arena.alloc(&q.excl, q.words));
+    if (out_delta_dev != nullptr) {
+        q.delta = out_delta_dev;
+    } else {
+        IMIN_CUDA(q.arena.alloc(&q.delta, g->n));
+    }
+    IMIN_CUDA(q.arena.alloc(&q.lists, 2ull * theta));
+    IMIN_CUDA(q.arena.alloc(&q.stats, kStCount));
+    IMIN_CUDA(q.arena.alloc(&q.scratch1, q.plan.scratch_bytes[1]));
+    IMIN_CUDA(q.arena.alloc(&q.scratch2, q.plan.scratch_bytes[2]));
+    IMIN_CUDA(cudaMemcpyAsync(q.seeds, seeds.data(), sizeof(int32_t) * seeds.size(),
+                              cudaMemcpyHostToDevice, s));
+    IMIN_CUDA(cudaMemsetAsync(q.excl, 0, sizeof(uint32_t) * q.words, s));
+    IMIN_CUDA(cudaMemsetAsync(q.delta, 0, sizeof(unsigned long long) * g->n, s));
+    IMIN_CUDA(cudaMemsetAsync(q.stats, 0, sizeof(unsigned long long) * kStCount, s));
+    IMIN_CUDA(cudaMemsetAsync(q.scratch1, 0xFF, q.plan.scratch_bytes[1], s));
+    IMIN_CUDA(cudaMemsetAsync(q.scratch2, 0xFF, q.plan.scratch_bytes[2], s));
+    IMIN_CUDA(launch_build_excl(q.excl, q.seeds, static_cast<int32_t>(seeds.size()), s));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return IMIN_OK;
+}
+
+// One Alg. 2 call: the three sample tiers in order.
+cudaError_t enqueue_call(const SampleParams& P, const Query& q, CallTimer& T)
+{
+    for (int t = 0; t < kTiers; ++t) {
+        uint8_t* scr = t == 1 ? q.scratch1 : (t == 2 ? q.scratch2 : nullptr);
+        const cudaError_t e = T.run(kKindTier0 + t, [&](bool* launched) {
+            return launch_sample_tier(t, P, q.plan, scr, T.s, launched);
+        });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_select(const SelectParams& sp, CallTimer& T)
+{
+    return T.run(kKindSelect, [&](bool* launched) {
+        *launched = true;
+        return launch_select(sp, T.s);
+    });
+}
+
+void record_stats(const unsigned long long* h)
+{
+    imin_stats& st = g_last_stats;
+    st = imin_stats{};
+    for (int t = 0; t < kTiers; ++t) {
+        const unsigned long long* x = h + t * kStPerTier;
+        st.samples += x[kStSamples];
+        st.reached += x[kStReached];
+        st.examined_edges += x[kStExamined];
+        st.live_edges += x[kStLive];
+        st.nontree_edges += x[kStNontree];
+        st.dom_passes += x[kStPasses];
+        st.tier_samples[t] = x[kStSamples];
+        st.tier_reached[t] = x[kStReached];
+        st.tier_examined_edges[t] = x[kStExamined];
+        st.tier_live_edges[t] = x[kStLive];
+    }
+}
+
+SampleParams sample_params(const imin_graph* g, const Query& q, uint32_t ns, uint32_t theta,
+                           uint64_t key, uint32_t round, RoundCtl* ctl, const int32_t* done)
+{
+    SampleParams P;
+    P.g = dev_graph(g);
+    P.seeds = q.seeds;
+    P.ns = ns;
+    P.excl = q.excl;
+    P.key_lo = static_cast<uint32_t>(key);
+    P.key_hi = static_cast<uint32_t>(key >> 32);
+    P.round = round;
+    P.theta = theta;
+    P.delta = q.delta;
+    P.ctl = ctl;
+    P.lists = q.lists;
+    P.done = done;
+    P.stats = q.stats;
+    return P;
+}
+
+int check_ctl(const std::vector<RoundCtl>& ctl)
+{
+    uint32_t err = 0;
+    for (const RoundCtl& c : ctl) err |= c.error;
+    if (err & kErrInternal) return fail(IMIN_ERR_INTERNAL, "dominator iteration did not converge");
+    if (err & kErrCapacity)
+        return fail(IMIN_ERR_CAPACITY, "a sampled cascade exceeded the largest tier's capacity");
+    return IMIN_OK;
+}
+
+int common_checks(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, uint32_t theta,
+                  cudaStream_t s, std::vector<int32_t>& hseeds, std::vector<uint8_t>& mark)
+{
+    if (g == nullptr) return fail(IMIN_ERR_INVALID, "graph handle is NULL");
+    if (n_seeds < 1 || n_seeds > g->n) return fail(IMIN_ERR_INVALID, "n_seeds must be in [1, n]");
+    if (theta < 1) return fail(IMIN_ERR_INVALID, "theta must be >= 1");
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(IMIN_ERR_CUDA, "cudaSetDevice failed");
+    int rc = to_host(seeds, n_seeds, hseeds, s, "seeds");
+    if (rc) return rc;
+    mark.assign(static_cast<size_t>(g->n), 0);
+    return check_ids(hseeds, g->n, mark, 1, "seeds");
+}
+
+int estimate_impl(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
+                  const int32_t* blocked, int32_t n_blocked, uint32_t theta, uint64_t key,
+                  uint32_t round, uint64_t* out_delta, imin_stats* stats, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int32_t> hseeds, hblocked;
+    std::vector<uint8_t> mark;
+    int rc = common_checks(g, seeds, n_seeds, theta, s, hseeds, mark);
+    if (rc) return rc;
+    if (out_delta == nullptr) return fail(IMIN_ERR_INVALID, "out_delta is NULL");
+    if (n_blocked < 0) return fail(IMIN_ERR_INVALID, "n_blocked must be >= 0");
+    rc = to_host(blocked, n_blocked, hblocked, s, "blocked");
+    if (rc) return rc;
+    rc = check_ids(hblocked, g->n, mark, 2, "blocked");
+    if (rc) return rc;
+
+    const bool dev_out = is_device_ptr(out_delta);
+    Query q(s);
+    rc = setup_query(g, hseeds, theta, dev_out ? reinterpret_cast<unsigned long long*>(out_delta) : nullptr, q);
+    if (rc) return rc;
+    RoundCtl* ctl = nullptr;
+    int32_t* dblocked = nullptr;
+    IMIN_CUDA(q.arena.alloc(&ctl, 1));
+    IMIN_CUDA(q.arena.alloc(&dblocked, hblocked.size()));
+    IMIN_CUDA(cudaMemsetAsync(ctl, 0, sizeof(RoundCtl), s));
+    if (!hblocked.empty()) {
+        IMIN_CUDA(cudaMemcpyAsync(dblocked, hblocked.data(), sizeof(int32_t) * hblocked.size(),
+                                  cudaMemcpyHostToDevice, s));
+        IMIN_CUDA(launch_build_excl(q.excl, dblocked, n_blocked, s));
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    CallTimer T(s);
+    const SampleParams P = sample_params(g, q, static_cast<uint32_t>(n_seeds), theta, key, round, ctl, nullptr);
+    IMIN_CUDA(enqueue_call(P, q, T));
+
+    std::vector<RoundCtl> hctl(1);
+    unsigned long long hstats[kStCount];
+    IMIN_CUDA(cudaMemcpyAsync(hctl.data(), ctl, sizeof(RoundCtl), cudaMemcpyDeviceToHost, s));
+    IMIN_CUDA(cudaMemcpyAsync(hstats, q.stats, sizeof(hstats), cudaMemcpyDeviceToHost, s));
+    if (!dev_out) {
+        IMIN_CUDA(cudaMemcpyAsync(out_delta, q.delta, sizeof(uint64_t) * g->n, cudaMemcpyDeviceToHost, s));
+    }
+    IMIN_CUDA(cudaStreamSynchronize(s));
+    T.collect();
+    rc = check_ctl(hctl);
+    if (rc) return rc;
+    record_stats(hstats);
+    if (stats != nullptr) *stats = g_last_stats;
+    return IMIN_OK;
+}
+
+enum class Driver { kAdvancedGreedy, kGreedyReplace };
+
+int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
+                int32_t b, uint32_t theta, uint64_t key, int32_t* out_blockers,
+                int32_t* out_count, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int32_t> hseeds;
+    std::vector<uint8_t> mark;
+    int rc = common_checks(g, seeds, n_seeds, theta, s, hseeds, mark);
+    if (rc) return rc;
+    if (b < 0) return fail(IMIN_ERR_INVALID, "b must be >= 0");
+    if (out_count == nullptr) return fail(IMIN_ERR_INVALID, "out_count is NULL");
+    if (b > 0 && out_blockers == nullptr) return fail(IMIN_ERR_INVALID, "out_blockers is NULL");
+    *out_count = 0;
+    if (b == 0) return IMIN_OK;
+
+    Query q(s);
+    rc = setup_query(g, hseeds, theta, nullptr, q);
+    if (rc) return rc;
+    int32_t* dB = nullptr;
+    int32_t* flags = nullptr;  // [0] = done, [1] = vertex unblocked in the current round
+    unsigned long long* part_d = nullptr;
+    int32_t* part_id = nullptr;
+    uint32_t* ticket = nullptr;
+    const int sel_blocks = select_blocks();
+    IMIN_CUDA(q.arena.alloc(&dB, static_cast<uint64_t>(b)));
+    IMIN_CUDA(q.arena.alloc(&flags, 2));
+    IMIN_CUDA(q.arena.alloc(&part_d, sel_blocks));
+    IMIN_CUDA(q.arena.alloc(&part_id, sel_blocks));
+    IMIN_CUDA(q.arena.alloc(&ticket, 1));
+    IMIN_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int32_t), s));
+    IMIN_CUDA(cudaMemsetAsync(ticket, 0, sizeof(uint32_t), s));
+
+    SelectParams sp{};
+    sp.delta = q.delta;
+    sp.n = g->n;
+    sp.excl = q.excl;
+    sp.blockers = dB;
+    sp.part_d = part_d;
+    sp.part_id = part_id;
+    sp.ticket = ticket;
+
+    int32_t count = 0;
+    std::vector<RoundCtl> hctl;
+    RoundCtl* ctl = nullptr;
+    CallTimer T(s);
+    if (which == Driver::kAdvancedGreedy) {
+        count = std::min<int32_t>(b, g->n - n_seeds);
+        if (count > 0) {
+            IMIN_CUDA(q.arena.alloc(&ctl, count));
+            IMIN_CUDA(cudaMemsetAsync(ctl, 0, sizeof(RoundCtl) * count, s));
+        }
+        for (int32_t i = 0; i < count; ++i) {
+            const SampleParams P = sample_params(g, q, n_seeds, theta, key, static_cast<uint32_t>(i),
+                                                 ctl + i, nullptr);
+            IMIN_CUDA(enqueue_call(P, q, T));
+            sp.pos = i;
+            IMIN_CUDA(enqueue_select(sp, T));
+        }
+        hctl.resize(count);
+    } else {
+        uint32_t* cb = nullptr;
+        uint32_t* cb_count = nullptr;
+        IMIN_CUDA(q.arena.alloc(&cb, q.words));
+        IMIN_CUDA(q.arena.alloc(&cb_count, 1));
+        IMIN_CUDA(cudaMemsetAsync(cb, 0, sizeof(uint32_t) * q.words, s));
+        IMIN_CUDA(cudaMemsetAsync(cb_count, 0, sizeof(uint32_t), s));
+        IMIN_CUDA(launch_build_cb(dev_graph(g), q.seeds, n_seeds, q.excl, cb, cb_count, s));
+        g_launches.fetch_add(2, std::memory_order_relaxed);
+        uint32_t hcb = 0;
+        IMIN_CUDA(cudaMemcpyAsync(&hcb, cb_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        IMIN_CUDA(cudaStreamSynchronize(s));
+        count = std::min<int32_t>(b, static_cast<int32_t>(hcb));
+        const int32_t calls = 2 * count;
+        if (calls > 0) {
+            IMIN_CUDA(q.arena.alloc(&ctl, calls));
+            IMIN_CUDA(cudaMemsetAsync(ctl, 0, sizeof(RoundCtl) * calls, s));
+        }
+        uint32_t round = 0;
+        // phase 1: greedy over the seeds' out-neighbours
+        for (int32_t i = 0; i < count; ++i, ++round) {
+            const SampleParams P = sample_params(g, q, n_seeds, theta, key, round, ctl + round, nullptr);
+            IMIN_CUDA(enqueue_call(P, q, T));
+            SelectParams p1 = sp;
+            p1.cand = cb;
+            p1.pos = i;
+            IMIN_CUDA(enqueue_select(p1, T));
+        }
+        // phase 2: replacements in reverse insertion order, stopping when a blocker stays
+        for (int32_t i = count - 1; i >= 0; --i, ++round) {
+            IMIN_CUDA(T.run(kKindOther, [&](bool* launched) {
+                *launched = true;
+                return launch_unblock(q.excl, dB, i, flags, flags + 1, s);
+            }));
+            const SampleParams P = sample_params(g, q, n_seeds, theta, key, round, ctl + round, flags);
+            IMIN_CUDA(enqueue_call(P, q, T));
+            SelectParams p2 = sp;
+            p2.pos = i;
+            p2.done = flags;
+            p2.cur = flags + 1;
+            IMIN_CUDA(enqueue_select(p2, T));
+        }
+        hctl.resize(calls);
+    }
+
+    std::vector<int32_t> hB(static_cast<size_t>(count));
+    unsigned long long hstats[kStCount];
+    IMIN_CUDA(cudaMemcpyAsync(hstats, q.stats, sizeof(hstats), cudaMemcpyDeviceToHost, s));
+    if (count > 0) {
+        IMIN_CUDA(cudaMemcpyAsync(hctl.data(), ctl, sizeof(RoundCtl) * hctl.size(), cudaMemcpyDeviceToHost, s));
+        IMIN_CUDA(cudaMemcpyAsync(hB.data(), dB, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s));
+    }
+    IMIN_CUDA(cudaStreamSynchronize(s));
+    T.collect();
+    rc = check_ctl(hctl);
+    if (rc) return rc;
+    record_stats(hstats);
+    if (count > 0) {
+        if (is_device_ptr(out_blockers)) {
+            IMIN_CUDA(cudaMemcpyAsync(out_blockers, dB, sizeof(int32_t) * count, cudaMemcpyDeviceToDevice, s));
+            IMIN_CUDA(cudaStreamSynchronize(s));
+        } else {
+            std::memcpy(out_blockers, hB.data(), sizeof(int32_t) * count);
+        }
+    }
+    *out_count = count;
+    return IMIN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int imin_abi_version(void) { return IMIN_ABI_VERSION; }
+
+const char* imin_last_error(void) { return g_err.c_str(); }
+
+int imin_load_graph(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t* col,
+                    const uint32_t* thr, void* stream, imin_graph** out)
+{
+    g_err.clear();
+    if (out == nullptr) return fail(IMIN_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n <= 0) return fail(IMIN_ERR_INVALID, "n must be > 0");
+    if (m < 0 || m >= (int64_t(1) << 31) - 4) return fail(IMIN_ERR_INVALID, "m must be in [0, 2^31 - 4)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int32_t> hrp, hcol;
+    std::vector<uint32_t> hthr;
+    int rc = to_host(row_ptr, static_cast<int64_t>(n) + 1, hrp, s, "row_ptr");
+    if (!rc) rc = to_host(col, m, hcol, s, "col");
+    if (!rc) rc = to_host(thr, m, hthr, s, "thr");
+    if (rc) return rc;
+    if (hrp[0] != 0 || hrp[n] != m) return fail(IMIN_ERR_INVALID, "row_ptr[0] must be 0 and row_ptr[n] == m");
+    for (int32_t u = 0; u < n; ++u)
+        if (hrp[u + 1] < hrp[u]) return fail(IMIN_ERR_INVALID, "row_ptr must be non-decreasing");
+    for (int64_t e = 0; e < m; ++e)
+        if (hcol[e] < 0 || hcol[e] >= n) return fail(IMIN_ERR_INVALID, "col entry out of range");
+
+    imin_graph* g = new imin_graph();
+    cudaGetDevice(&g->device);
+    g->dev = device_info();
+    g->n = n;
+    g->m = static_cast<int32_t>(m);
+    keep_pool_memory(g->device);
+    const int64_t m4 = ((m + 3) / 4) * 4 + 4;  // padded so the last 16-byte group is in bounds
+    hcol.resize(m4, 0);
+    hthr.resize(m4, 0);
+    cudaError_t e = cudaMalloc(&g->row_ptr, sizeof(int32_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->col, sizeof(int32_t) * m4);
+    if (e == cudaSuccess) e = cudaMalloc(&g->thr4, sizeof(uint32_t) * m4);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->row_ptr, hrp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->col, hcol.data(), sizeof(int32_t) * m4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->thr4, hthr.data(), sizeof(uint32_t) * m4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        imin_free_graph(g);
+        return fail_cuda(e, "imin_load_graph");
+    }
+    *out = g;
+    return IMIN_OK;
+}
+
+int imin_free_graph(imin_graph* g)
+{
+    if (g == nullptr) return IMIN_OK;
+    cudaFree(g->row_ptr);
+    cudaFree(g->col);
+    cudaFree(g->thr4);
+    delete g;
+    return IMIN_OK;
+}
+
+int imin_graph_info(const imin_graph* g, int32_t* n, int64_t* m)
+{
+    if (g == nullptr) return fail(IMIN_ERR_INVALID, "graph handle is NULL");
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    return IMIN_OK;
+}
+
+uint64_t imin_launch_count(void) { return g_launches.load(); }
+
+int imin_last_stats(imin_stats* out)
+{
+    if (out == nullptr) return fail(IMIN_ERR_INVALID, "out is NULL");
+    *out = g_last_stats;
+    return IMIN_OK;
+}
+
+int imin_profile_enable(int on)
+{
+    g_profile_on.store(on != 0);
+    return IMIN_OK;
+}
+
+int imin_profile_read(imin_profile* out, int reset)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (out != nullptr) {
+        for (int k = 0; k < kKinds; ++k) {
+            out->launches[k] = g_prof_launches[k];
+            out->ms[k] = g_prof_ms[k];
+        }
+    }
+    if (reset) {
+        for (int k = 0; k < kKinds; ++k) {
+            g_prof_launches[k] = 0;
+            g_prof_ms[k] = 0.0;
+        }
+    }
+    return IMIN_OK;
+}
+
+int imin_estimate_decrease(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
+                           const int32_t* blocked, int32_t n_blocked, uint32_t theta,
+                           uint64_t key, uint32_t round, uint64_t* out_delta, void* stream)
+{
+    g_err.clear();
+    return estimate_impl(g, seeds, n_seeds, blocked, n_blocked, theta, key, round, out_delta,
+                         nullptr, stream);
+}
+
+int imin_estimate_decrease_stats(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
+                                 const int32_t* blocked, int32_t n_blocked, uint32_t theta,
+                                 uint64_t key, uint32_t round, uint64_t* out_delta,
+                                 imin_stats* stats, void* stream)
+{
+    g_err.clear();
+    return estimate_impl(g, seeds, n_seeds, blocked, n_blocked, theta, key, round, out_delta,
+                         stats, stream);
+}
+
+int imin_advanced_greedy(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b,
+                         uint32_t theta, uint64_t key, int32_t* out_blockers, int32_t* out_count,
+                         void* stream)
+{
+    g_err.clear();
+    return greedy_impl(Driver::kAdvancedGreedy, g, seeds, n_seeds, b, theta, key, out_blockers,
+                       out_count, stream);
+}
+
+int imin_greedy_replace(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b,
+                        uint32_t theta, uint64_t key, int32_t* out_blockers, int32_t* out_count,
+                        void* stream)
+{
+    g_err.clear();
+    return greedy_impl(Driver::kGreedyReplace, g, seeds, n_seeds, b, theta, key, out_blockers,
+                       out_count, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,421 @@
+// imin_dev.cuh -- device-side pieces of the sampled-dominator-tree estimator (Alg. 2 of
+// arXiv 2302.13529) for sm_103a.
+//
+// One warp owns one sampled graph (Def. 4) at a time and runs, without ever materialising
+// the sampled graph:
+//   1. a level-synchronous BFS from the seeds (all at depth 0 under a virtual super-seed,
+//      Sec. 4 "From Multiple Seeds to One Seed"). The out-edges of a frontier are flattened
+//      into groups of 4 consecutive edge ids; each lane takes one group, loads its 4
+//      thresholds with one 16-byte load, evaluates one Philox4x32-10 call whose 4 output words
+//      decide the 4 edges, and loads the target id only for live edges. Live targets that are
+//      neither seeds nor blocked go through a warp-shared open-addressing hash (global id ->
+//      local id). A newly inserted vertex gets the next local id, so local ids follow BFS
+//      discovery order and every level occupies a contiguous id range; the discovering vertex
+//      becomes its initial dominator candidate. Live edges to already-known vertices are kept
+//      as "non-tree" edges.
+//   2. immediate dominators (Defs. 5-6) by the iterative intersection scheme of Cooper,
+//      Harvey and Kennedy on BFS numbering: start from the BFS tree and, for every non-tree
+//      edge (p, v), lower idom(v) to the nearest common ancestor of idom(v), p and v's BFS
+//      parent in the current tree, until a pass changes nothing. A dominator of v lies on
+//      every path to v, in particular on a shortest one, so it has a smaller BFS number and
+//      the tree always satisfies idom(v) < v. Why the result is the dominator tree: the
+//      ancestor sets X(v) start as BFS-tree paths, which contain every dominator, and each
+//      update keeps them supersets of the dominator sets; at the end every in-edge (p, v)
+//      -- the parent edge included, which is why it is folded in every pass -- has idom(v)
+//      above p, so X is a post-fixed point of the dominance equations, hence contained in
+//      their greatest fixed point, the dominator sets. Both inclusions give equality.
+//   3. subtree sizes (Thm. 6) by one sweep over BFS levels from the deepest up (a dominator
+//      is strictly shallower than what it dominates), adding each size into its idom.
+//   4. Delta[u] += c[u] for every reached non-seed u (64-bit atomics into global memory).
+//
+// The warp's working set lives either in shared memory (tier 0) or in a per-warp global
+// scratch slot (tiers 1 and 2, bigger capacities). A sample that exceeds its tier's capacity
+// is abandoned (its hash entries are cleared) and handed to the next tier; nothing it
+// computed has been published, so the retry is exact.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace imin {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr int kTiers = 3;
+constexpr int kStageCap = 128;  // 32 lanes x 4 edges per group
+
+enum : uint32_t { kErrCapacity = 1u, kErrInternal = 2u };
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 3.3). Counter c, key (k0, k1).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+struct DevGraph {
+    int32_t n;
+    int32_t m;
+    const int32_t* __restrict__ row_ptr;  // [n+1]
+    const int32_t* __restrict__ col;      // [m], padded to a multiple of 4
+    const uint4* __restrict__ thr4;       // [ceil(m/4)] thresholds, 4 per vector
+};
+
+// Control block of one Alg. 2 call (zeroed before it starts).
+struct RoundCtl {
+    uint32_t cursor[kTiers];  // next work item of each tier
+    uint32_t count[kTiers];   // samples handed to tier t (t >= 1)
+    uint32_t error;           // kErr* bits
+    uint32_t pad;
+};
+
+// Stats slots (unsigned long long each), kStPerTier per tier: stats[tier * kStPerTier + slot].
+enum { kStSamples = 0, kStReached, kStExamined, kStLive, kStNontree, kStPasses, kStPerTier,
+       kStCount = kStPerTier * kTiers };
+
+struct SampleParams {
+    DevGraph g;
+    const int32_t* seeds;          // [ns]
+    uint32_t ns;
+    const uint32_t* excl;          // n-bit mask: seeds and blocked vertices
+    uint32_t key_lo, key_hi;
+    uint32_t round;
+    uint32_t theta;
+    unsigned long long* delta;     // [n]
+    RoundCtl* ctl;
+    uint32_t* lists;               // [2*theta]: tier-1 input list, tier-2 input list
+    const int32_t* done;           // optional stop flag (GreedyReplace phase 2)
+    unsigned long long* stats;     // optional [kStCount] (per-tier slots)
+};
+
+// Capacities of one tier's per-warp working set.
+struct TierCfg {
+    uint32_t rcap;   // local ids incl. the super-seed (0) and the seeds
+    uint32_t hcap;   // hash slots, power of two, >= 2 * rcap
+    uint32_t hbits;  // log2(hcap)
+    uint32_t ecap;   // non-tree edges
+    uint32_t dcap;   // BFS levels
+    uint8_t* gscratch;      // tiers 1-2: per-warp slots
+    uint64_t warp_bytes;    // bytes per slot (tier 0: shared memory per warp)
+    uint32_t from_range;    // take samples [0, theta) directly (first tier that runs)
+};
+
+// Byte layout of one warp's working set (same for shared and global memory).
+struct WarpLayout {
+    uint64_t lvl, hkey, hval, gid, idom, par, hslot, edges, total;
+};
+
+__host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
+
+__host__ __device__ inline WarpLayout warp_layout(uint32_t rcap, uint32_t hcap, uint32_t ecap,
+                                                 uint32_t dcap, bool with_hslot)
+{
+    WarpLayout L;
+    uint64_t o = 0;
+    L.lvl = o;   o = align16(o + 4ull * (dcap + 1));
+    L.hkey = o;  o = align16(o + 4ull * hcap);
+    L.hval = o;  o = align16(o + 4ull * (hcap > rcap ? hcap : rcap));  // doubles as c[]
+    L.gid = o;   o = align16(o + 4ull * rcap);
+    L.idom = o;  o = align16(o + 4ull * rcap);
+    L.par = o;   o = align16(o + 4ull * rcap);
+    L.hslot = o; o = align16(o + (with_hslot ? 4ull * rcap : 0));
+    L.edges = o; o = align16(o + 8ull * ecap);
+    L.total = o;
+    return L;
+}
+
+template <bool G>
+struct WarpSpace {
+    uint32_t* lvl;
+    uint32_t* hkey;
+    uint32_t* hval;
+    int32_t* gid;
+    uint32_t* idom;
+    uint32_t* par;   // BFS parent (idom before the dominator passes)
+    uint32_t* hslot;
+    uint2* edges;
+    uint2* stage;  // always shared memory, kStageCap entries
+    uint32_t rcap, hcap, hbits, ecap, dcap;
+};
+
+// Loads of words that other lanes update with atomics or stores during the same sample.
+// Global scratch is read through L2 (.cg) so that no stale L1 line is ever used.
+template <bool G>
+__device__ __forceinline__ uint32_t ld_shared_word(const uint32_t* p)
+{
+    if constexpr (G) {
+        return __ldcg(p);
+    } else {
+        return *reinterpret_cast<const volatile uint32_t*>(p);
+    }
+}
+
+struct SampleCounters {
+    unsigned long long reached = 0, examined = 0, live = 0, nontree = 0, passes = 0, done = 0;
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, uint32_t lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, x, o);
+        if (lane >= static_cast<uint32_t>(o)) x += t;
+    }
+    return x;
+}
+
+__device__ __forceinline__ bool excluded(const uint32_t* excl, uint32_t v)
+{
+    return (__ldg(excl + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+enum SampleResult { kSampleDone = 0, kSampleOverflow = 1, kSampleError = 2 };
+
+// Runs sample j of call P.round in warp space w. kClearAll: reset the whole hash afterwards
+// (small shared tables) instead of the slots recorded in hslot[].
+template <bool G, bool kClearAll>
+__device__ __forceinline__ int run_sample(const SampleParams& P, const WarpSpace<G>& w,
+                                          uint32_t j, uint32_t lane, SampleCounters& sc)
+{
+    const uint32_t ns = P.ns;
+    const uint32_t hmask = w.hcap - 1;
+    const uint32_t hshift = 32 - w.hbits;
+
+    for (uint32_t i = lane; i < ns; i += 32) {
+        w.gid[1 + i] = P.seeds[i];
+        w.idom[1 + i] = 0;
+        w.par[1 + i] = 0;
+    }
+    if (lane == 0) {
+        w.idom[0] = 0;
+        w.lvl[0] = 1;
+        w.lvl[1] = 1 + ns;
+    }
+    __syncwarp();
+
+    uint32_t nR = 1 + ns;  // local ids in use (warp-uniform)
+    uint32_t nE = 0;       // non-tree edges
+    uint32_t nlev = 1;     // completed levels; level d = [lvl[d], lvl[d+1])
+    bool over = false;
+    unsigned long long examined = 0, live = 0;
+
+    uint32_t lb = 1, le = 1 + ns;
+    while (lb < le) {
+        for (uint32_t base = lb; base < le && !over; base += 32) {
+            // ---- the frontier vertices of this chunk and their edge groups
+            const uint32_t idx = base + lane;
+            int32_t beg = 0, end = 0;
+            if (idx < le) {
+                const int32_t u = w.gid[idx];
+                beg = __ldg(P.g.row_ptr + u);
+                end = __ldg(P.g.row_ptr + u + 1);
+            }
+            examined += static_cast<uint32_t>(end - beg);
+            const uint32_t ng =
+                end > beg ? (static_cast<uint32_t>(end - 1) >> 2) - (static_cast<uint32_t>(beg) >> 2) + 1
+                          : 0u;
+            const uint32_t incl = warp_incl_scan(ng, lane);
+            const uint32_t total = __shfl_sync(kFull, incl, 31);
+
+            for (uint32_t t0 = 0; t0 < total && !over; t0 += 32) {
+                const uint32_t t = t0 + lane;
+                // owner lane: the first lane whose inclusive group count exceeds t
+                uint32_t pos = 0;
+#pragma unroll
+                for (uint32_t step = 16; step >= 1; step >>= 1) {
+                    const uint32_t v = __shfl_sync(kFull, incl, pos + step - 1);
+                    if (v <= t) pos += step;
+                }
+                const uint32_t o_incl = __shfl_sync(kFull, incl, pos);
+                const uint32_t o_ng = __shfl_sync(kFull, ng, pos);
+                const int32_t o_beg = __shfl_sync(kFull, beg, pos);
+                const int32_t o_end = __shfl_sync(kFull, end, pos);
+
+                bool ok0 = false, ok1 = false, ok2 = false, ok3 = false;
+                uint32_t v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+                const uint32_t ul = base + pos;
+                if (t < total) {
+                    const uint32_t q = (static_cast<uint32_t>(o_beg) >> 2) + (t - (o_incl - o_ng));
+                    const uint4 th = __ldg(P.g.thr4 + q);
+                    const uint4 r = philox4x32_10(make_uint4(q, j, P.round, 0u), P.key_lo, P.key_hi);
+                    const int32_t e0 = static_cast<int32_t>(q << 2);
+                    ok0 = (e0 + 0 >= o_beg) && (e0 + 0 < o_end) && (r.x <= th.x);
+                    ok1 = (e0 + 1 >= o_beg) && (e0 + 1 < o_end) && (r.y <= th.y);
+                    ok2 = (e0 + 2 >= o_beg) && (e0 + 2 < o_end) && (r.z <= th.z);
+                    ok3 = (e0 + 3 >= o_beg) && (e0 + 3 < o_end) && (r.w <= th.w);
+                    if (ok0) { v0 = static_cast<uint32_t>(__ldg(P.g.col + e0 + 0)); ok0 = !excluded(P.excl, v0); }
+                    if (ok1) { v1 = static_cast<uint32_t>(__ldg(P.g.col + e0 + 1)); ok1 = !excluded(P.excl, v1); }
+                    if (ok2) { v2 = static_cast<uint32_t>(__ldg(P.g.col + e0 + 2)); ok2 = !excluded(P.excl, v2); }
+                    if (ok3) { v3 = static_cast<uint32_t>(__ldg(P.g.col + e0 + 3)); ok3 = !excluded(P.excl, v3); }
+                }
+                const uint32_t nc = (uint32_t)ok0 + (uint32_t)ok1 + (uint32_t)ok2 + (uint32_t)ok3;
+                live += nc;
+                const uint32_t cincl = warp_incl_scan(nc, lane);
+                const uint32_t ctot = __shfl_sync(kFull, cincl, 31);
+                if (ctot == 0) continue;
+                {
+                    uint32_t p = cincl - nc;
+                    if (ok0) w.stage[p++] = make_uint2(ul, v0);
+                    if (ok1) w.stage[p++] = make_uint2(ul, v1);
+                    if (ok2) w.stage[p++] = make_uint2(ul, v2);
+                    if (ok3) w.stage[p++] = make_uint2(ul, v3);
+                }
+                __syncwarp();
+
+                // ---- insert the staged live targets, one per lane per step
+                for (uint32_t s0 = 0; s0 < ctot; s0 += 32) {
+                    const bool act = s0 + lane < ctot;
+                    uint32_t st = 0, slot = 0, cu = 0, cv = 0;
+                    if (act) {
+                        const uint2 c = w.stage[s0 + lane];
+                        cu = c.x;
+                        cv = c.y;
+                        slot = (cv * 0x9E3779B1u) >> hshift;
+                        for (uint32_t probe = 0; probe < w.hcap; ++probe) {
+                            const uint32_t k = ld_shared_word<G>(w.hkey + slot);
+                            if (k == cv) { st = 2; break; }
+                            if (k == kEmpty) {
+                                const uint32_t prev = atomicCAS(w.hkey + slot, kEmpty, cv);
+                                if (prev == kEmpty) { st = 1; break; }
+                                if (prev == cv) { st = 2; break; }
+                            }
+                            slot = (slot + 1) & hmask;
+                        }
+                    }
+                    const uint32_t won = __ballot_sync(kFull, st == 1);
+                    const uint32_t lid = nR + __popc(won & lanemask_lt());
+                    bool bad = act && st == 0;  // table full: cannot happen below capacity
+                    if (st == 1) {
+                        if (lid < w.rcap) {
+                            w.hval[slot] = lid;
+                            w.gid[lid] = static_cast<int32_t>(cv);
+                            w.idom[lid] = cu;
+                            w.par[lid] = cu;
+                            if constexpr (!kClearAll) w.hslot[lid] = slot;
+                        } else {
+                            w.hkey[slot] = kEmpty;  // this lane owns the slot; undo it
+                            bad = true;
+                        }
+                    }
+                    nR += __popc(won);
+                    __syncwarp();
+                    bool nt = false;
+                    uint32_t vl = 0;
+                    if (st == 2) {
+                        vl = ld_shared_word<G>(w.hval + slot);
+                        nt = vl != cu;  // a self-loop never matters
+                    }
+                    const uint32_t ntm = __ballot_sync(kFull, nt);
+                    const uint32_t epos = nE + __popc(ntm & lanemask_lt());
+                    if (nt && epos < w.ecap) w.edges[epos] = make_uint2(cu, vl);
+                    nE += __popc(ntm);
+                    if (__any_sync(kFull, bad) || nE > w.ecap || nR > w.rcap) over = true;
+                }
+                __syncwarp();
+            }
+        }
+        if (over) break;
+        if (nR > le) {
+            if (nlev + 1 > w.dcap) { over = true; break; }
+            if (lane == 0) w.lvl[nlev + 1] = nR;
+            ++nlev;
+        }
+        lb = le;
+        le = nR;
+        __syncwarp();
+    }
+
+    if (over) {
+        // abandon: clear every hash slot this sample used
+        if constexpr (kClearAll) {
+            for (uint32_t i = lane; i < w.hcap; i += 32) w.hkey[i] = kEmpty;
+        } else {
+            const uint32_t lim = nR < w.rcap ? nR : w.rcap;
+            for (uint32_t i = 1 + ns + lane; i < lim; i += 32) w.hkey[w.hslot[i]] = kEmpty;
+        }
+        __syncwarp();
+        return kSampleOverflow;
+    }
+
+    // ---- immediate dominators: iterate NCA(idom(v), p) over non-tree edges to the fixed point
+    uint32_t passes = 0;
+    bool broken = false;
+    if (nE > 0) {
+        for (;;) {
+            bool changed = false;
+            for (uint32_t k = lane; k < nE; k += 32) {
+                const uint2 e = w.edges[k];
+                uint32_t a = ld_shared_word<G>(w.idom + e.y);
+                uint32_t b = e.x;
+                // both chains strictly decrease towards the super-seed (id 0)
+                for (uint32_t guard = 0; a != b; ++guard) {
+                    if (guard > 2 * nR) { broken = true; a = 0; break; }
+                    if (a > b) a = ld_shared_word<G>(w.idom + a);
+                    else b = ld_shared_word<G>(w.idom + b);
+                }
+                b = w.par[e.y];
+                for (uint32_t guard = 0; a != b; ++guard) {
+                    if (guard > 2 * nR) { broken = true; a = 0; break; }
+                    if (a > b) a = ld_shared_word<G>(w.idom + a);
+                    else b = ld_shared_word<G>(w.idom + b);
+                }
+                if (!broken && a < ld_shared_word<G>(w.idom + e.y)) {
+                    const uint32_t old = atomicMin(w.idom + e.y, a);
+                    changed |= a < old;
+                }
+            }
+            ++passes;
+            broken = __any_sync(kFull, broken);
+            if (broken || !__any_sync(kFull, changed)) break;
+            if (passes > nR + 1) { broken = true; break; }  // a monotone descent cannot take longer
+        }
+    }
+    __syncwarp();
+
+    // ---- subtree sizes, deepest level first
+    uint32_t* c = w.hval;
+    for (uint32_t i = lane; i < nR; i += 32) c[i] = 1;
+    __syncwarp();
+    for (uint32_t d = nlev - 1; d >= 1; --d) {
+        const uint32_t b0 = w.lvl[d], b1 = w.lvl[d + 1];
+        for (uint32_t i = b0 + lane; i < b1; i += 32)
+            atomicAdd(c + ld_shared_word<G>(w.idom + i), ld_shared_word<G>(c + i));
+        __syncwarp();
+    }
+
+    // ---- publish: Delta[u] += c[u] for reached non-seeds; then clear the hash
+    for (uint32_t i = 1 + ns + lane; i < nR; i += 32)
+        atomicAdd(P.delta + w.gid[i], static_cast<unsigned long long>(ld_shared_word<G>(c + i)));
+    if constexpr (kClearAll) {
+        for (uint32_t i = lane; i < w.hcap; i += 32) w.hkey[i] = kEmpty;
+    } else {
+        for (uint32_t i = 1 + ns + lane; i < nR; i += 32) w.hkey[w.hslot[i]] = kEmpty;
+    }
+    __syncwarp();
+
+    sc.reached += nR - 1;
+    sc.examined += examined;
+    sc.live += live;
+    sc.nontree += nE;
+    sc.passes += passes;
+    sc.done += 1;
+    return broken ? kSampleError : kSampleDone;
+}
+
+}  // namespace imin

@@ -1,0 +1,67 @@
+// internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <cuda_runtime.h>
+
+#include "imin_dev.cuh"
+
+namespace imin {
+
+// Launch shape and capacities of the three sample tiers for one graph / seed-set size.
+struct TierPlan {
+    TierCfg cfg[kTiers];
+    uint32_t warps_per_block[kTiers];
+    uint32_t blocks[kTiers];
+    uint64_t smem_bytes[kTiers];  // dynamic shared memory per block
+    uint64_t scratch_bytes[kTiers];
+};
+
+struct DeviceInfo {
+    int device = 0;
+    int sms = 0;
+    uint64_t smem_optin = 0;
+};
+
+DeviceInfo device_info();
+
+// Tier capacities for a graph with n vertices and m edges and a seed set of size ns.
+TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns);
+
+// Enqueue tier `tier` of one Alg. 2 call (tier 0 takes samples [0, theta); tiers 1 and 2 take
+// the samples the previous tier could not hold). P.ctl must be zeroed and P.delta cleared
+// before tier 0; `scratch` must point at plan.scratch_bytes[tier] bytes whose hash words are
+// all 0xFF (tiers 1-2). Returns cudaSuccess without launching when the tier has no blocks.
+// *launched is set to whether a kernel was enqueued.
+cudaError_t launch_sample_tier(int tier, const SampleParams& P, const TierPlan& plan,
+                               uint8_t* scratch, cudaStream_t s, bool* launched);
+
+// Selection (Alg. 3/4 argmax) -----------------------------------------------------------------
+struct SelectParams {
+    unsigned long long* delta;     // [n]; cleared as it is read
+    int32_t n;
+    uint32_t* excl;                // n-bit mask; the winner is added
+    uint32_t* cand;                // optional n-bit candidate mask (GreedyReplace phase 1);
+                                   // when null the candidates are the vertices not in excl.
+                                   // The winner is removed from it.
+    int32_t* blockers;             // the winner is written to blockers[pos]
+    int32_t pos;
+    int32_t* done;                 // optional stop flag
+    const int32_t* cur;            // optional: vertex unblocked for this round; winner == *cur
+                                   // sets *done
+    unsigned long long* part_d;    // [blocks] scratch
+    int32_t* part_id;              // [blocks] scratch
+    uint32_t* ticket;              // zero-initialised counter
+};
+
+int select_blocks();
+cudaError_t launch_select(const SelectParams& p, cudaStream_t s);
+cudaError_t launch_unblock(uint32_t* excl, const int32_t* blockers, int32_t pos, const int32_t* done,
+                           int32_t* cur, cudaStream_t s);
+cudaError_t launch_build_excl(uint32_t* excl, const int32_t* ids, int32_t count, cudaStream_t s);
+cudaError_t launch_build_cb(const DevGraph& g, const int32_t* seeds, int32_t ns,
+                            const uint32_t* excl, uint32_t* cb, uint32_t* cb_count,
+                            cudaStream_t s);
+
+}  // namespace imin

@@ -1,0 +1,220 @@
+// sample.cu -- the three sample tiers of Alg. 2 (DecreaseESComputation) and their planning.
+//
+// Tier 0 keeps each warp's working set in shared memory and takes every sample first.
+// A sample whose cascade outgrows shared memory is re-run by tier 1 from a per-warp slot of
+// global scratch with capacity for 16K reached vertices; tier 2 holds any cascade (|R| <= n)
+// and is launched with few warps, because its slots scale with n. Work is handed out by an
+// atomic cursor per tier, so warps that draw small cascades keep pulling new samples.
+#include <algorithm>
+#include <cstdlib>
+
+#include "internal.h"
+
+namespace imin {
+
+namespace {
+
+constexpr uint32_t kWarpsPerBlock = 8;
+constexpr uint32_t kStageBytes = kStageCap * sizeof(uint2);
+
+uint32_t next_pow2(uint64_t x)
+{
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return static_cast<uint32_t>(p);
+}
+
+uint32_t log2u(uint32_t p)
+{
+    uint32_t b = 0;
+    while ((1u << b) < p) ++b;
+    return b;
+}
+
+uint32_t env_u32(const char* name, uint32_t dflt)
+{
+    const char* v = std::getenv(name);
+    if (!v || !*v) return dflt;
+    return static_cast<uint32_t>(std::strtoul(v, nullptr, 10));
+}
+
+template <int kTier>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_sample_tier(SampleParams P, TierCfg T)
+{
+    constexpr bool G = kTier > 0;
+    constexpr bool kClearAll = kTier == 0;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t wib = threadIdx.x >> 5;
+    const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+
+    if (P.done != nullptr && *reinterpret_cast<const volatile int32_t*>(P.done) != 0) return;
+
+    const uint64_t smem_per_warp = kStageBytes + (G ? 0 : T.warp_bytes);
+    uint8_t* my_smem = smem + wib * smem_per_warp;
+    uint8_t* base = G ? T.gscratch + gw * T.warp_bytes : my_smem + kStageBytes;
+    const WarpLayout L = warp_layout(T.rcap, T.hcap, T.ecap, T.dcap, !kClearAll);
+
+    WarpSpace<G> w;
+    w.stage = reinterpret_cast<uint2*>(my_smem);
+    w.lvl = reinterpret_cast<uint32_t*>(base + L.lvl);
+    w.hkey = reinterpret_cast<uint32_t*>(base + L.hkey);
+    w.hval = reinterpret_cast<uint32_t*>(base + L.hval);
+    w.gid = reinterpret_cast<int32_t*>(base + L.gid);
+    w.idom = reinterpret_cast<uint32_t*>(base + L.idom);
+    w.par = reinterpret_cast<uint32_t*>(base + L.par);
+    w.hslot = reinterpret_cast<uint32_t*>(base + L.hslot);
+    w.edges = reinterpret_cast<uint2*>(base + L.edges);
+    w.rcap = T.rcap;
+    w.hcap = T.hcap;
+    w.hbits = T.hbits;
+    w.ecap = T.ecap;
+    w.dcap = T.dcap;
+
+    if constexpr (!G) {
+        for (uint32_t i = lane; i < w.hcap; i += 32) w.hkey[i] = kEmpty;
+        __syncwarp();
+    }
+
+    SampleCounters sc;
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(&P.ctl->cursor[kTier], 1u);
+        item = __shfl_sync(kFull, item, 0);
+        const bool from_range = kTier == 0 || T.from_range != 0;
+        const uint32_t total =
+            from_range ? P.theta : *reinterpret_cast<const volatile uint32_t*>(&P.ctl->count[kTier]);
+        if (item >= total) break;
+        const uint32_t j = from_range ? item : P.lists[(kTier - 1) * P.theta + item];
+        const int rc = run_sample<G, kClearAll>(P, w, j, lane, sc);
+        if (rc == kSampleOverflow) {
+            if (lane == 0) {
+                if (kTier + 1 < kTiers) {
+                    const uint32_t pos = atomicAdd(&P.ctl->count[kTier + 1], 1u);
+                    P.lists[kTier * P.theta + pos] = j;
+                } else {
+                    atomicOr(&P.ctl->error, kErrCapacity);
+                }
+            }
+        } else if (rc == kSampleError) {
+            if (lane == 0) atomicOr(&P.ctl->error, kErrInternal);
+        }
+    }
+
+    if (P.stats != nullptr) {
+        unsigned long long ex = sc.examined, lv = sc.live;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            ex += __shfl_down_sync(kFull, ex, o);
+            lv += __shfl_down_sync(kFull, lv, o);
+        }
+        if (lane == 0 && sc.done > 0) {
+            unsigned long long* st = P.stats + kTier * kStPerTier;
+            atomicAdd(st + kStSamples, sc.done);
+            atomicAdd(st + kStReached, sc.reached);
+            atomicAdd(st + kStExamined, ex);
+            atomicAdd(st + kStLive, lv);
+            atomicAdd(st + kStNontree, sc.nontree);
+            atomicAdd(st + kStPasses, sc.passes);
+        }
+    }
+}
+
+}  // namespace
+
+DeviceInfo device_info()
+{
+    DeviceInfo d;
+    cudaGetDevice(&d.device);
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, d.device);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d.device);
+    d.smem_optin = static_cast<uint64_t>(optin);
+    return d;
+}
+
+TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns)
+{
+    TierPlan p{};
+    const uint32_t r0 = env_u32("IMIN_TIER0_VERTICES", 256);    // non-seed capacity, tier 0
+    const uint32_t r1 = env_u32("IMIN_TIER1_VERTICES", 16384);  // non-seed capacity, tier 1
+    const uint32_t b1 = env_u32("IMIN_TIER1_BLOCKS_PER_SM", 2);
+    const uint64_t t2_budget = static_cast<uint64_t>(env_u32("IMIN_TIER2_MIB", 4096)) << 20;
+
+    // tier 0: shared memory
+    {
+        TierCfg& c = p.cfg[0];
+        c.rcap = 1 + ns + r0;
+        c.hcap = next_pow2(2ull * std::max<uint32_t>(r0, 32));  // load <= 1/2 + 32 in flight
+        c.hbits = log2u(c.hcap);
+        c.ecap = std::max<uint32_t>(r0 / 2, 32);
+        c.dcap = 64;
+        c.warp_bytes = warp_layout(c.rcap, c.hcap, c.ecap, c.dcap, false).total;
+        c.gscratch = nullptr;
+        p.warps_per_block[0] = kWarpsPerBlock;
+        p.smem_bytes[0] = kWarpsPerBlock * (kStageBytes + c.warp_bytes);
+        p.scratch_bytes[0] = 0;
+        int occ = 0;
+        if (p.smem_bytes[0] <= dev.smem_optin) {
+            cudaFuncSetAttribute(k_sample_tier<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(p.smem_bytes[0]));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_tier<0>,
+                                                          kWarpsPerBlock * 32, p.smem_bytes[0]);
+        }
+        p.blocks[0] = static_cast<uint32_t>(std::max(occ, 0)) * dev.sms;
+    }
+    // tier 1: per-warp global slot for up to r1 non-seed vertices
+    {
+        TierCfg& c = p.cfg[1];
+        const uint32_t r = std::min<uint64_t>(r1, static_cast<uint64_t>(n));
+        c.rcap = 1 + ns + r;
+        c.hcap = next_pow2(2ull * std::max<uint32_t>(r, 32));
+        c.hbits = log2u(c.hcap);
+        c.ecap = std::max<uint32_t>(r / 4, 256);
+        c.dcap = std::min<uint32_t>(c.rcap, 1024);
+        c.warp_bytes = (warp_layout(c.rcap, c.hcap, c.ecap, c.dcap, true).total + 255) & ~255ull;
+        p.warps_per_block[1] = kWarpsPerBlock;
+        p.blocks[1] = b1 * dev.sms;
+        p.smem_bytes[1] = kWarpsPerBlock * kStageBytes;
+        p.scratch_bytes[1] = c.warp_bytes * p.blocks[1] * kWarpsPerBlock;
+    }
+    // tier 2: per-warp global slot for any cascade (|R| <= n)
+    {
+        TierCfg& c = p.cfg[2];
+        c.rcap = 1 + static_cast<uint32_t>(n);
+        c.hcap = next_pow2(2ull * std::max<uint64_t>(static_cast<uint64_t>(n), 32));
+        c.hbits = log2u(c.hcap);
+        c.ecap = static_cast<uint32_t>(std::max<int64_t>(std::min<int64_t>(m, 4ll * n), 1024));
+        c.dcap = c.rcap;
+        c.warp_bytes = (warp_layout(c.rcap, c.hcap, c.ecap, c.dcap, true).total + 255) & ~255ull;
+        uint64_t warps = std::max<uint64_t>(1, t2_budget / c.warp_bytes);
+        warps = std::min<uint64_t>(warps, static_cast<uint64_t>(dev.sms) * kWarpsPerBlock);
+        const uint32_t blocks = static_cast<uint32_t>((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
+        p.warps_per_block[2] = kWarpsPerBlock;
+        p.blocks[2] = blocks;
+        p.smem_bytes[2] = kWarpsPerBlock * kStageBytes;
+        p.scratch_bytes[2] = c.warp_bytes * blocks * kWarpsPerBlock;
+    }
+    return p;
+}
+
+cudaError_t launch_sample_tier(int tier, const SampleParams& P, const TierPlan& plan,
+                               uint8_t* scratch, cudaStream_t s, bool* launched)
+{
+    *launched = false;
+    if (plan.blocks[tier] == 0) return cudaSuccess;
+    TierCfg c = plan.cfg[tier];
+    c.gscratch = scratch;
+    // the first tier that runs takes the whole sample range; tier 0 is skipped only when the
+    // seed set does not fit its shared-memory working set
+    c.from_range = tier == 0 || (tier == 1 && plan.blocks[0] == 0);
+    const dim3 grid(plan.blocks[tier]), block(kWarpsPerBlock * 32);
+    if (tier == 0) k_sample_tier<0><<<grid, block, plan.smem_bytes[0], s>>>(P, c);
+    else if (tier == 1) k_sample_tier<1><<<grid, block, plan.smem_bytes[1], s>>>(P, c);
+    else k_sample_tier<2><<<grid, block, plan.smem_bytes[2], s>>>(P, c);
+    *launched = true;
+    return cudaGetLastError();
+}
+
+}  // namespace imin

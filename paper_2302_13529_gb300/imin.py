@@ -1,0 +1,208 @@
+"""Python binding of the CUDA C-ABI library (include/imin.h): argument marshalling only.
+
+Every entry point takes the same arguments as its C counterpart. Arrays may be numpy arrays
+(host memory) or torch tensors (host or CUDA); device work is enqueued on the current torch
+CUDA stream unless a stream handle is given. There is no CPU fallback: if libimin.so is not
+built or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+IMIN_OK = 0
+ERRORS = {-1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
+          -4: "capacity exceeded", -5: "internal error"}
+
+_lib = None
+
+
+class IminError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("samples", ctypes.c_uint64), ("reached", ctypes.c_uint64),
+                ("examined_edges", ctypes.c_uint64), ("live_edges", ctypes.c_uint64),
+                ("nontree_edges", ctypes.c_uint64), ("dom_passes", ctypes.c_uint64),
+                ("tier_samples", ctypes.c_uint64 * 3), ("tier_reached", ctypes.c_uint64 * 3),
+                ("tier_examined_edges", ctypes.c_uint64 * 3),
+                ("tier_live_edges", ctypes.c_uint64 * 3)]
+
+    def as_dict(self):
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = [int(x) for x in v] if k.startswith("tier_") else int(v)
+        return d
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64 * 5), ("ms", ctypes.c_double * 5)]
+
+
+KINDS = ("sample_tier0", "sample_tier1", "sample_tier2", "select", "other")
+
+
+def lib():
+    """Load libimin.so (built by paper_2302_13529_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is not built; run paper_2302_13529_gb300.build.build()")
+        L = ctypes.CDLL(LIB)
+        P = ctypes.c_void_p
+        L.imin_load_graph.argtypes = [ctypes.c_int32, ctypes.c_int64, P, P, P, P,
+                                      ctypes.POINTER(P)]
+        L.imin_free_graph.argtypes = [P]
+        L.imin_graph_info.argtypes = [P, P, P]
+        L.imin_estimate_decrease.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int32,
+                                             ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                             P, P]
+        L.imin_estimate_decrease_stats.argtypes = L.imin_estimate_decrease.argtypes[:-1] + [
+            ctypes.POINTER(Stats), P]
+        for name in ("imin_advanced_greedy", "imin_greedy_replace"):
+            getattr(L, name).argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
+                                         ctypes.c_uint64, P, P, P]
+        L.imin_last_stats.argtypes = [ctypes.POINTER(Stats)]
+        L.imin_launch_count.restype = ctypes.c_uint64
+        L.imin_profile_enable.argtypes = [ctypes.c_int]
+        L.imin_profile_read.argtypes = [ctypes.POINTER(Profile), ctypes.c_int]
+        L.imin_last_error.restype = ctypes.c_char_p
+        L.imin_abi_version.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != IMIN_OK:
+        raise IminError(rc, lib().imin_last_error().decode())
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(a, dtype):
+    """(pointer, keep-alive object, length) for a numpy array or torch tensor."""
+    if a is None:
+        return None, None, 0
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+        want = {np.int32: torch.int32, np.uint32: torch.uint32, np.uint64: torch.uint64}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return ctypes.c_void_p(a.data_ptr()), a, a.numel()
+    arr = np.ascontiguousarray(np.asarray(a), dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), arr, arr.size
+
+
+class GraphHandle:
+    """A graph resident in device memory (imin_load_graph / imin_free_graph)."""
+
+    def __init__(self, n, row_ptr, col, thr, stream=None):
+        rp, k1, _ = _ptr(row_ptr, np.int32)
+        c, k2, m = _ptr(col, np.int32)
+        t, k3, _ = _ptr(thr, np.uint32)
+        h = ctypes.c_void_p()
+        _check(lib().imin_load_graph(int(n), int(m), rp, c, t, _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.n = int(n)
+        self.m = int(m)
+
+    @classmethod
+    def from_graph(cls, g, stream=None):
+        return cls(g.n, g.row_ptr, g.col, g.thr, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().imin_free_graph(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def load_graph(g, stream=None) -> GraphHandle:
+    return GraphHandle.from_graph(g, stream)
+
+
+def estimate_decrease(gh: GraphHandle, seeds, blocked, theta, key, round_=0, out=None,
+                      stream=None, stats=False):
+    """imin_estimate_decrease: uint64 counters Delta[n] (numpy unless `out` is given)."""
+    s, ks, ns = _ptr(seeds, np.int32)
+    b, kb, nb = _ptr(blocked if blocked is not None and len(blocked) else None, np.int32)
+    if out is None:
+        out = np.zeros(gh.n, dtype=np.uint64)
+    o, ko, _ = _ptr(out, np.uint64)
+    if stats:
+        st = Stats()
+        _check(lib().imin_estimate_decrease_stats(gh.handle, s, ns, b, nb, int(theta), int(key),
+                                                  int(round_), o, ctypes.byref(st),
+                                                  _stream(stream)))
+        return out, st.as_dict()
+    _check(lib().imin_estimate_decrease(gh.handle, s, ns, b, nb, int(theta), int(key),
+                                        int(round_), o, _stream(stream)))
+    return out
+
+
+def _greedy(fn, gh, seeds, b, theta, key, out, stream):
+    s, ks, ns = _ptr(seeds, np.int32)
+    if out is None:
+        out = np.zeros(max(int(b), 1), dtype=np.int32)
+    o, ko, _ = _ptr(out, np.int32)
+    cnt = ctypes.c_int32()
+    _check(fn(gh.handle, s, ns, int(b), int(theta), int(key), o, ctypes.byref(cnt),
+              _stream(stream)))
+    return out[:cnt.value]
+
+
+def advanced_greedy(gh: GraphHandle, seeds, b, theta, key, out=None, stream=None):
+    """imin_advanced_greedy (Alg. 3): blockers in selection order."""
+    return _greedy(lib().imin_advanced_greedy, gh, seeds, b, theta, key, out, stream)
+
+
+def greedy_replace(gh: GraphHandle, seeds, b, theta, key, out=None, stream=None):
+    """imin_greedy_replace (Alg. 4): blockers in list order."""
+    return _greedy(lib().imin_greedy_replace, gh, seeds, b, theta, key, out, stream)
+
+
+# ---- measurement hooks ---------------------------------------------------------------------
+
+def last_stats() -> dict:
+    """Work counters of the last estimate / greedy call on this thread (imin_last_stats)."""
+    st = Stats()
+    _check(lib().imin_last_stats(ctypes.byref(st)))
+    return st.as_dict()
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far (imin_launch_count)."""
+    return int(lib().imin_launch_count())
+
+
+def profile_enable(on: bool = True) -> None:
+    _check(lib().imin_profile_enable(1 if on else 0))
+
+
+def profile_read(reset: bool = False) -> dict:
+    """Per-kind {launches, ms} accumulated while profiling was enabled (imin_profile_read)."""
+    p = Profile()
+    _check(lib().imin_profile_read(ctypes.byref(p), 1 if reset else 0))
+    return {k: {"launches": int(p.launches[i]), "ms": float(p.ms[i])} for i, k in enumerate(KINDS)}

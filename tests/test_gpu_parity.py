@@ -1,0 +1,193 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle, bit for bit.
+
+All arithmetic on the path is integer (Philox words, threshold compares, subtree sizes and
+uint64 sums), so the tolerance is zero: counters and blockers must be identical.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2302_13529_gb300 import workloads as W
+from tests import oracle_pool
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_case(i):
+    rng = np.random.default_rng(1000 + i)
+    n = int(rng.integers(5, 40))
+    m = int(rng.integers(n, 4 * n))
+    g = W.random_small_graph(n, m, seed=2000 + i)
+    k = int(rng.integers(1, min(5, n)))
+    seeds = [int(x) for x in rng.choice(n, k, replace=False)]
+    rest = [v for v in range(n) if v not in seeds]
+    nb = int(rng.integers(0, min(4, len(rest)) + 1))
+    blocked = [int(x) for x in rng.choice(rest, nb, replace=False)] if nb else []
+    return g, seeds, blocked
+
+
+@pytest.mark.parametrize("i", range(16))
+def test_decrease_small_graphs(cuda_lib, i):
+    g, seeds, blocked = _small_case(i)
+    gh = cuda_lib.load_graph(g)
+    for theta, key, rnd in ((1, 5, 0), (37, 77, 3), (2000, 0xDEADBEEFCAFE, 11)):
+        want = O.decrease(g, seeds, blocked, theta, key, rnd)
+        got = cuda_lib.estimate_decrease(gh, seeds, blocked, theta, key, rnd)
+        assert np.array_equal(got, want), (i, theta)
+
+
+def test_toy_graph_counters(cuda_lib):
+    from tests.test_oracle_pins import TOY
+    gh = cuda_lib.load_graph(TOY)
+    for key in (1, 99):
+        want = O.decrease(TOY, [0], [], 50_000, key)
+        got = cuda_lib.estimate_decrease(gh, [0], [], 50_000, key)
+        assert np.array_equal(got, want)
+    assert list(cuda_lib.advanced_greedy(gh, [0], 2, 20_000, 3)) == [4, 1]
+    assert sorted(cuda_lib.greedy_replace(gh, [0], 2, 20_000, 3)) == [1, 3]
+    assert list(cuda_lib.greedy_replace(gh, [0], 1, 20_000, 3)) == [4]
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return W.tiny_chung_lu_query()
+
+
+def test_decrease_chung_lu(cuda_lib, tiny):
+    q = tiny
+    gh = cuda_lib.load_graph(q.graph)
+    blocked = [int(x) for x in np.setdiff1d(np.arange(60), q.seeds)[:7]]
+    for rnd, bl in ((0, []), (4, blocked)):
+        want = O.decrease(q.graph, q.seeds, bl, q.theta, q.key, rnd)
+        got, st = cuda_lib.estimate_decrease(gh, q.seeds, bl, q.theta, q.key, rnd, stats=True)
+        assert np.array_equal(got, want)
+        assert st["samples"] == q.theta
+
+
+def test_advanced_greedy_chung_lu(cuda_lib, tiny):
+    q = tiny
+    gh = cuda_lib.load_graph(q.graph)
+    want = O.advanced_greedy(q.graph, q.seeds, q.b, q.theta, q.key)
+    got = cuda_lib.advanced_greedy(gh, q.seeds, q.b, q.theta, q.key)
+    assert np.array_equal(got, want)
+
+
+def test_greedy_replace_chung_lu(cuda_lib, tiny):
+    q = tiny
+    gh = cuda_lib.load_graph(q.graph)
+    want = O.greedy_replace(q.graph, q.seeds, q.b, q.theta, q.key)
+    got = cuda_lib.greedy_replace(gh, q.seeds, q.b, q.theta, q.key)
+    assert np.array_equal(got, want)
+
+
+def test_tier_fallback_paths(cuda_lib, monkeypatch):
+    """Tiny tier capacities push samples through all three tiers; results must not change."""
+    g = W.graph_rmat_wc(11, 16000, seed=5)
+    seeds = W.uniform_seeds(g.n, 12, seed=6)
+    want = O.decrease(g, seeds, [], 3000, 1234, 2)
+    gh = cuda_lib.load_graph(g)
+    monkeypatch.setenv("IMIN_TIER0_VERTICES", "32")
+    monkeypatch.setenv("IMIN_TIER1_VERTICES", "64")
+    got, st = cuda_lib.estimate_decrease(gh, seeds, [], 3000, 1234, 2, stats=True)
+    assert np.array_equal(got, want)
+    assert st["tier_samples"][1] > 0 and st["tier_samples"][2] > 0, st
+    assert sum(st["tier_samples"]) == 3000
+    monkeypatch.delenv("IMIN_TIER0_VERTICES")
+    monkeypatch.delenv("IMIN_TIER1_VERTICES")
+    got2 = cuda_lib.estimate_decrease(gh, seeds, [], 3000, 1234, 2)
+    assert np.array_equal(got2, want)
+
+
+def test_device_pointers_and_determinism(cuda_lib, tiny):
+    import torch
+    q = tiny
+    gh = cuda_lib.load_graph(q.graph)
+    seeds_d = torch.from_numpy(q.seeds).cuda()
+    out = torch.zeros(q.graph.n, dtype=torch.uint64, device="cuda")
+    cuda_lib.estimate_decrease(gh, seeds_d, None, 5000, q.key, 1, out=out)
+    torch.cuda.synchronize()
+    want = O.decrease(q.graph, q.seeds, [], 5000, q.key, 1)
+    assert np.array_equal(out.cpu().numpy(), want)
+    again = cuda_lib.estimate_decrease(gh, q.seeds, [], 5000, q.key, 1)
+    assert np.array_equal(again, want)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        third = cuda_lib.estimate_decrease(gh, q.seeds, [], 5000, q.key, 1)
+    assert np.array_equal(third, want)
+    blk = torch.zeros(q.b, dtype=torch.int32, device="cuda")
+    cuda_lib.advanced_greedy(gh, seeds_d, q.b, 2000, q.key, out=blk)
+    assert np.array_equal(blk.cpu().numpy(), O.advanced_greedy(q.graph, q.seeds, q.b, 2000, q.key))
+
+
+def test_edge_cases(cuda_lib):
+    g = W.graph_from_edges(6, [(0, 1, 1), (1, 2, 1), (2, 0, 1), (3, 4, W.Fraction(1, 2))])
+    gh = cuda_lib.load_graph(g)
+    # an isolated seed reaches nothing
+    assert not cuda_lib.estimate_decrease(gh, [5], [], 100, 1).any()
+    # a cycle back into the seed is ignored
+    d = cuda_lib.estimate_decrease(gh, [0], [], 10, 1)
+    assert list(d) == [0, 20, 10, 0, 0, 0]
+    # every vertex but one is a seed
+    d = cuda_lib.estimate_decrease(gh, [0, 1, 2, 3, 4], [], 64, 9)
+    assert np.array_equal(d, O.decrease(g, [0, 1, 2, 3, 4], [], 64, 9))
+    # AG stops when the candidates run out; GR with no out-neighbours returns nothing
+    assert sorted(cuda_lib.advanced_greedy(gh, [0, 1, 2], 10, 20, 1)) == [3, 4, 5]
+    assert len(cuda_lib.greedy_replace(gh, [5], 3, 20, 1)) == 0
+    assert len(cuda_lib.advanced_greedy(gh, [0], 0, 20, 1)) == 0
+    # graph without edges
+    g0 = W.Graph(3, np.zeros(4, np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint32))
+    gh0 = cuda_lib.load_graph(g0)
+    assert not cuda_lib.estimate_decrease(gh0, [1], [], 5, 1).any()
+
+
+def test_invalid_arguments(cuda_lib):
+    from paper_2302_13529_gb300.imin import IminError
+    g = W.graph_from_edges(4, [(0, 1, 1), (1, 2, 1)])
+    gh = cuda_lib.load_graph(g)
+    for seeds, blocked in (([0, 0], []), ([0], [0]), ([4], []), ([0], [1, 1]), ([-1], [])):
+        with pytest.raises(IminError) as e:
+            cuda_lib.estimate_decrease(gh, seeds, blocked, 10, 1)
+        assert e.value.code == -1
+    with pytest.raises(IminError):
+        cuda_lib.estimate_decrease(gh, [0], [], 0, 1)
+    with pytest.raises(IminError):
+        cuda_lib.GraphHandle(3, np.array([0, 1, 0, 1], np.int32), np.array([1], np.int32),
+                             np.array([5], np.uint32))
+
+
+# --------------------------------------------------------------------------------------------
+# full-size workload: R-MAT 2^17 / 2^20, WC, |S| = 50, theta = 10^5 (bench configuration)
+# --------------------------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def rmat17():
+    return W.rmat17_query()
+
+
+def test_full_size_round_counters(cuda_lib, rmat17):
+    """One complete Alg. 2 call at full size (theta = 10^5), every counter compared."""
+    q = rmat17
+    gh = cuda_lib.load_graph(q.graph)
+    got, st = cuda_lib.estimate_decrease(gh, q.seeds, [], q.theta, q.key, 0, stats=True)
+    want = oracle_pool.decrease(q.graph, q.seeds, [], q.theta, q.key, 0)
+    assert np.array_equal(got, want)
+    assert st["samples"] == q.theta
+
+
+def test_full_size_advanced_greedy_sampled_rounds(cuda_lib, rmat17):
+    """AG at full size; rounds 0, 1 and b-1 replayed by the oracle from the GPU's prefix:
+    the blocker of round i must be the oracle's argmax given B[:i]."""
+    q = rmat17
+    gh = cuda_lib.load_graph(q.graph)
+    B = cuda_lib.advanced_greedy(gh, q.seeds, q.b, q.theta, q.key)
+    assert len(B) == q.b and len(set(B.tolist())) == q.b
+    assert not set(B.tolist()) & set(q.seeds.tolist())
+    for i in (0, 1, q.b - 1):
+        d = oracle_pool.decrease(q.graph, q.seeds, B[:i], q.theta, q.key, i).astype(np.int64)
+        d[q.seeds] = -1
+        d[B[:i]] = -1
+        assert int(np.argmax(d)) == int(B[i]), i
