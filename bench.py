@@ -320,7 +320,7 @@ def main(argv=None):
     ms_per_step = 1e3 * slowest / args.steps
 
     # roofline of the dominant kernel (the sample tier with the most device time)
-    tiers = [("sample_tier0", 0), ("sample_tier1", 1), ("sample_tier2", 2)]
+    tiers = [("sample_tier0", 0), ("sample_tier1", 1), ("sample_tier2", 2), ("sample_cta", 3)]
     kname, tier = max(tiers, key=lambda kt: prof[kt[0]]["ms"])
     kp = prof[kname]
     avg_ms = kp["ms"] / max(kp["launches"], 1)
@@ -333,9 +333,10 @@ def main(argv=None):
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(f"k_sample_tier{tier}")
+    kfn = "k_sample_cta" if tier == 3 else f"k_sample_tier{tier}"
+    traffic = ncu_traffic(kfn)
     total_ms = sum(v["ms"] for v in prof.values())
-    roofline = {"kernel": f"k_sample_tier<{tier}>", "bound": "hbm", "achieved": achieved,
+    roofline = {"kernel": kfn, "bound": "hbm", "achieved": achieved,
                 "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": avg_ms, "share_of_device_time": kp["ms"] / max(total_ms, 1e-9),

@@ -118,12 +118,14 @@ typedef struct imin_stats {
     uint64_t live_edges;     /* sum over samples of live edges into reached non-seed vertices */
     uint64_t nontree_edges;  /* live edges that were not BFS discovery edges */
     uint64_t dom_passes;     /* dominator fixed-point passes */
-    /* per kernel tier (0: shared-memory working set, 1: per-warp global scratch for up to 16K
-       reached vertices, 2: whole-graph scratch), counting the samples each tier finished */
-    uint64_t tier_samples[3];
-    uint64_t tier_reached[3];
-    uint64_t tier_examined_edges[3];
-    uint64_t tier_live_edges[3];
+    /* per kernel tier, counting the samples each tier finished: 0 = warp per sample with a
+       shared-memory hash, 1 = warp per sample with global scratch for up to 16K reached
+       vertices, 2 = warp per sample with whole-graph scratch (final fallback), 3 = block per
+       sample with a shared-memory visited bitmap (graphs with n <= 2^18) */
+    uint64_t tier_samples[4];
+    uint64_t tier_reached[4];
+    uint64_t tier_examined_edges[4];
+    uint64_t tier_live_edges[4];
 } imin_stats;
 
 /* imin_estimate_decrease plus the work counters of the call. Synchronizes `stream`. */
@@ -143,13 +145,12 @@ uint64_t imin_launch_count(void);
 
 /* Per-kind kernel timing. When enabled, every kernel launch of the entry points above is
  * bracketed by CUDA events recorded on the stream it is launched on; the elapsed times are
- * added up when the entry point synchronizes. Kinds: 0-2 = sample tiers 0-2, 3 = blocker
- * selection, 4 = other small kernels (only launches of kind 4 made by the greedy drivers are
- * timed). Timing adds event records between launches; leave it off when measuring
- * whole-call throughput. */
+ * added up when the entry point synchronizes. Kinds: 0-3 = sample tiers 0-3, 4 = blocker
+ * selection, 5 = other small kernels (only launches of kind 5 made by the greedy drivers are
+ * timed). Timing adds event records between launches. */
 typedef struct imin_profile {
-    uint64_t launches[5];
-    double ms[5];
+    uint64_t launches[6];
+    double ms[6];
 } imin_profile;
 int imin_profile_enable(int on);
 int imin_profile_read(imin_profile* out, int reset);

@@ -53,7 +53,7 @@ int fail_cuda(cudaError_t e, const char* where)
 
 // ---- measurement hooks (not part of the method) -------------------------------------------
 // Kernel kinds: the three sample tiers, the selection, everything else.
-enum Kind { kKindTier0 = 0, kKindTier1, kKindTier2, kKindSelect, kKindOther, kKinds };
+enum Kind { kKindTier0 = 0, kKindTier1, kKindTier2, kKindCta, kKindSelect, kKindOther, kKinds };
 
 std::atomic<uint64_t> g_launches{0};
 std::atomic<int> g_profile_on{0};
@@ -202,6 +202,7 @@ struct Query {
     unsigned long long* stats = nullptr;
     uint8_t* scratch1 = nullptr;
     uint8_t* scratch2 = nullptr;
+    uint8_t* scratch3 = nullptr;
     int32_t words = 0;
     explicit Query(cudaStream_t s) : arena(s) {}
 };
@@ -219,10 +220,11 @@ int setup_query(const imin_graph* g, const std::vector<int32_t>& seeds, uint32_t
     } else {
         IMIN_CUDA(q.arena.alloc(&q.delta, g->n));
     }
-    IMIN_CUDA(q.arena.alloc(&q.lists, 2ull * theta));
+    IMIN_CUDA(q.arena.alloc(&q.lists, static_cast<uint64_t>(kTiers) * theta));
     IMIN_CUDA(q.arena.alloc(&q.stats, kStCount));
     IMIN_CUDA(q.arena.alloc(&q.scratch1, q.plan.scratch_bytes[1]));
     IMIN_CUDA(q.arena.alloc(&q.scratch2, q.plan.scratch_bytes[2]));
+    IMIN_CUDA(q.arena.alloc(&q.scratch3, q.plan.scratch_bytes[kTierCta]));
     IMIN_CUDA(cudaMemcpyAsync(q.seeds, seeds.data(), sizeof(int32_t) * seeds.size(),
                               cudaMemcpyHostToDevice, s));
     IMIN_CUDA(cudaMemsetAsync(q.excl, 0, sizeof(uint32_t) * q.words, s));
@@ -235,12 +237,19 @@ int setup_query(const imin_graph* g, const std::vector<int32_t>& seeds, uint32_t
     return IMIN_OK;
 }
 
-// One Alg. 2 call: the three sample tiers in order.
+// One Alg. 2 call: the sample tiers in order (3 then 2 when the block-per-sample tier
+// applies, otherwise 0, 1, 2).
 cudaError_t enqueue_call(const SampleParams& P, const Query& q, CallTimer& T)
 {
-    for (int t = 0; t < kTiers; ++t) {
-        uint8_t* scr = t == 1 ? q.scratch1 : (t == 2 ? q.scratch2 : nullptr);
-        const cudaError_t e = T.run(kKindTier0 + t, [&](bool* launched) {
+    static const int kWarpOrder[] = {0, 1, 2};
+    static const int kCtaOrder[] = {kTierCta, kTierWhole};
+    const int* order = q.plan.use_cta ? kCtaOrder : kWarpOrder;
+    const int count = q.plan.use_cta ? 2 : 3;
+    for (int k = 0; k < count; ++k) {
+        const int t = order[k];
+        uint8_t* scr = t == 1 ? q.scratch1 : (t == 2 ? q.scratch2 : (t == kTierCta ? q.scratch3 : nullptr));
+        const int kind = t == kTierCta ? kKindCta : kKindTier0 + t;
+        const cudaError_t e = T.run(kind, [&](bool* launched) {
             return launch_sample_tier(t, P, q.plan, scr, T.s, launched);
         });
         if (e != cudaSuccess) return e;

@@ -41,7 +41,13 @@ namespace imin {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
-constexpr int kTiers = 3;
+// Tiers: 0-2 are warp-per-sample (0: shared-memory hash, 1: per-warp global hash for up to
+// 16K vertices, 2: per-warp whole-graph scratch, the final fallback); 3 is block-per-sample with
+// a shared-memory visited bitmap (graphs with n <= kCtaMaxVertices).
+constexpr int kTiers = 4;
+constexpr int kTierWhole = 2;
+constexpr int kTierCta = 3;
+constexpr int32_t kCtaMaxVertices = 1 << 18;
 constexpr int kStageCap = 128;  // 32 lanes x 4 edges per group
 
 enum : uint32_t { kErrCapacity = 1u, kErrInternal = 2u };
@@ -92,7 +98,7 @@ struct SampleParams {
     uint32_t theta;
     unsigned long long* delta;     // [n]
     RoundCtl* ctl;
-    uint32_t* lists;               // [2*theta]: tier-1 input list, tier-2 input list
+    uint32_t* lists;               // [kTiers*theta]: input list of tier t at lists + t*theta
     const int32_t* done;           // optional stop flag (GreedyReplace phase 2)
     unsigned long long* stats;     // optional [kStCount] (per-tier slots)
 };
@@ -107,6 +113,17 @@ struct TierCfg {
     uint8_t* gscratch;      // tiers 1-2: per-warp slots
     uint64_t warp_bytes;    // bytes per slot (tier 0: shared memory per warp)
     uint32_t from_range;    // take samples [0, theta) directly (first tier that runs)
+};
+
+// Block-per-sample tier (sample_cta.cu): per-block slot layout and shared-memory sizes.
+struct CtaCfg {
+    uint32_t bm_words;    // visited bitmap words (>= n/32), also the resolution hash space
+    uint32_t res_slots;   // resolution hash slots (power of two; keys + values fit in bm_words)
+    uint32_t res_shift;   // 32 - log2(res_slots)
+    uint32_t rcap;        // local ids per slot (n + 1: never exceeded)
+    uint32_t ecap;        // non-tree edges per slot
+    uint64_t off_gid, off_par, off_idom, off_edges, slot_bytes;
+    uint8_t* scratch;
 };
 
 // Byte layout of one warp's working set (same for shared and global memory).

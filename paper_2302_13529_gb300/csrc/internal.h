@@ -16,6 +16,8 @@ struct TierPlan {
     uint32_t blocks[kTiers];
     uint64_t smem_bytes[kTiers];  // dynamic shared memory per block
     uint64_t scratch_bytes[kTiers];
+    bool use_cta = false;         // tier 3 replaces tiers 0 and 1
+    CtaCfg cta{};
 };
 
 struct DeviceInfo {
@@ -36,6 +38,12 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns);
 // *launched is set to whether a kernel was enqueued.
 cudaError_t launch_sample_tier(int tier, const SampleParams& P, const TierPlan& plan,
                                uint8_t* scratch, cudaStream_t s, bool* launched);
+
+// Block-per-sample tier (graphs with n <= kCtaMaxVertices): layout, grid and shared memory.
+bool plan_cta_tier(const DeviceInfo& dev, int32_t n, CtaCfg* c, uint32_t* blocks, uint64_t* smem,
+                   uint64_t* scratch_bytes);
+cudaError_t launch_cta_tier(const SampleParams& P, const CtaCfg& c, uint32_t blocks, uint64_t smem,
+                            uint8_t* scratch, cudaStream_t s);
 
 // Selection (Alg. 3/4 argmax) -----------------------------------------------------------------
 struct SelectParams {

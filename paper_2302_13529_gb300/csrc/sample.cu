@@ -86,13 +86,13 @@ k_sample_tier(SampleParams P, TierCfg T)
         const uint32_t total =
             from_range ? P.theta : *reinterpret_cast<const volatile uint32_t*>(&P.ctl->count[kTier]);
         if (item >= total) break;
-        const uint32_t j = from_range ? item : P.lists[(kTier - 1) * P.theta + item];
+        const uint32_t j = from_range ? item : P.lists[kTier * P.theta + item];
         const int rc = run_sample<G, kClearAll>(P, w, j, lane, sc);
         if (rc == kSampleOverflow) {
             if (lane == 0) {
-                if (kTier + 1 < kTiers) {
+                if (kTier < kTierWhole) {
                     const uint32_t pos = atomicAdd(&P.ctl->count[kTier + 1], 1u);
-                    P.lists[kTier * P.theta + pos] = j;
+                    P.lists[(kTier + 1) * P.theta + pos] = j;
                 } else {
                     atomicOr(&P.ctl->error, kErrCapacity);
                 }
@@ -140,7 +140,17 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns)
     const uint32_t r0 = env_u32("IMIN_TIER0_VERTICES", 256);    // non-seed capacity, tier 0
     const uint32_t r1 = env_u32("IMIN_TIER1_VERTICES", 16384);  // non-seed capacity, tier 1
     const uint32_t b1 = env_u32("IMIN_TIER1_BLOCKS_PER_SM", 2);
-    const uint64_t t2_budget = static_cast<uint64_t>(env_u32("IMIN_TIER2_MIB", 4096)) << 20;
+    const bool allow_cta = env_u32("IMIN_DISABLE_CTA_TIER", 0) == 0;
+    uint64_t t2_budget = static_cast<uint64_t>(env_u32("IMIN_TIER2_MIB", 4096)) << 20;
+
+    // tier 3: block per sample with a shared-memory visited bitmap, whenever n allows
+    if (allow_cta && plan_cta_tier(dev, n, &p.cta, &p.blocks[kTierCta], &p.smem_bytes[kTierCta],
+                                   &p.scratch_bytes[kTierCta])) {
+        p.use_cta = true;
+        p.warps_per_block[kTierCta] = 4;
+        // tier 2 only catches the rare samples with too many non-tree edges or levels
+        t2_budget = std::min<uint64_t>(t2_budget, 1ull << 30);
+    }
 
     // tier 0: shared memory
     {
@@ -162,7 +172,7 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_tier<0>,
                                                           kWarpsPerBlock * 32, p.smem_bytes[0]);
         }
-        p.blocks[0] = static_cast<uint32_t>(std::max(occ, 0)) * dev.sms;
+        p.blocks[0] = p.use_cta ? 0u : static_cast<uint32_t>(std::max(occ, 0)) * dev.sms;
     }
     // tier 1: per-warp global slot for up to r1 non-seed vertices
     {
@@ -175,7 +185,7 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns)
         c.dcap = std::min<uint32_t>(c.rcap, 1024);
         c.warp_bytes = (warp_layout(c.rcap, c.hcap, c.ecap, c.dcap, true).total + 255) & ~255ull;
         p.warps_per_block[1] = kWarpsPerBlock;
-        p.blocks[1] = b1 * dev.sms;
+        p.blocks[1] = p.use_cta ? 0u : b1 * dev.sms;
         p.smem_bytes[1] = kWarpsPerBlock * kStageBytes;
         p.scratch_bytes[1] = c.warp_bytes * p.blocks[1] * kWarpsPerBlock;
     }
@@ -204,11 +214,15 @@ cudaError_t launch_sample_tier(int tier, const SampleParams& P, const TierPlan& 
 {
     *launched = false;
     if (plan.blocks[tier] == 0) return cudaSuccess;
+    if (tier == kTierCta) {
+        *launched = true;
+        return launch_cta_tier(P, plan.cta, plan.blocks[kTierCta], plan.smem_bytes[kTierCta], scratch, s);
+    }
     TierCfg c = plan.cfg[tier];
     c.gscratch = scratch;
     // the first tier that runs takes the whole sample range; tier 0 is skipped only when the
     // seed set does not fit its shared-memory working set
-    c.from_range = tier == 0 || (tier == 1 && plan.blocks[0] == 0);
+    c.from_range = tier == 0 || (tier == 1 && plan.blocks[0] == 0 && !plan.use_cta);
     const dim3 grid(plan.blocks[tier]), block(kWarpsPerBlock * 32);
     if (tier == 0) k_sample_tier<0><<<grid, block, plan.smem_bytes[0], s>>>(P, c);
     else if (tier == 1) k_sample_tier<1><<<grid, block, plan.smem_bytes[1], s>>>(P, c);

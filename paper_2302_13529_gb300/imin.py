@@ -31,9 +31,9 @@ class Stats(ctypes.Structure):
     _fields_ = [("samples", ctypes.c_uint64), ("reached", ctypes.c_uint64),
                 ("examined_edges", ctypes.c_uint64), ("live_edges", ctypes.c_uint64),
                 ("nontree_edges", ctypes.c_uint64), ("dom_passes", ctypes.c_uint64),
-                ("tier_samples", ctypes.c_uint64 * 3), ("tier_reached", ctypes.c_uint64 * 3),
-                ("tier_examined_edges", ctypes.c_uint64 * 3),
-                ("tier_live_edges", ctypes.c_uint64 * 3)]
+                ("tier_samples", ctypes.c_uint64 * 4), ("tier_reached", ctypes.c_uint64 * 4),
+                ("tier_examined_edges", ctypes.c_uint64 * 4),
+                ("tier_live_edges", ctypes.c_uint64 * 4)]
 
     def as_dict(self):
         d = {}
@@ -44,10 +44,10 @@ class Stats(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint64 * 5), ("ms", ctypes.c_double * 5)]
+    _fields_ = [("launches", ctypes.c_uint64 * 6), ("ms", ctypes.c_double * 6)]
 
 
-KINDS = ("sample_tier0", "sample_tier1", "sample_tier2", "select", "other")
+KINDS = ("sample_tier0", "sample_tier1", "sample_tier2", "sample_cta", "select", "other")
 
 
 def lib():

@@ -84,22 +84,44 @@ def test_greedy_replace_chung_lu(cuda_lib, tiny):
     assert np.array_equal(got, want)
 
 
-def test_tier_fallback_paths(cuda_lib, monkeypatch):
-    """Tiny tier capacities push samples through all three tiers; results must not change."""
+@pytest.mark.parametrize("path", ["warp-tiers", "block-tier-overflow"])
+def test_tier_fallback_paths(cuda_lib, monkeypatch, path):
+    """Tiny capacities push samples through every tier of a pipeline; results must not change.
+    warp-tiers: shared-memory hash -> 16K global scratch -> whole-graph scratch;
+    block-tier-overflow: block-per-sample bitmap tier -> whole-graph scratch."""
     g = W.graph_rmat_wc(11, 16000, seed=5)
     seeds = W.uniform_seeds(g.n, 12, seed=6)
     want = O.decrease(g, seeds, [], 3000, 1234, 2)
     gh = cuda_lib.load_graph(g)
-    monkeypatch.setenv("IMIN_TIER0_VERTICES", "32")
-    monkeypatch.setenv("IMIN_TIER1_VERTICES", "64")
+    if path == "warp-tiers":
+        monkeypatch.setenv("IMIN_DISABLE_CTA_TIER", "1")
+        monkeypatch.setenv("IMIN_TIER0_VERTICES", "32")
+        monkeypatch.setenv("IMIN_TIER1_VERTICES", "64")
+        used = (0, 1, 2)
+    else:
+        monkeypatch.setenv("IMIN_CTA_EDGE_CAP", "2")
+        used = (3, 2)
     got, st = cuda_lib.estimate_decrease(gh, seeds, [], 3000, 1234, 2, stats=True)
     assert np.array_equal(got, want)
-    assert st["tier_samples"][1] > 0 and st["tier_samples"][2] > 0, st
+    assert all(st["tier_samples"][t] > 0 for t in used), st
     assert sum(st["tier_samples"]) == 3000
-    monkeypatch.delenv("IMIN_TIER0_VERTICES")
-    monkeypatch.delenv("IMIN_TIER1_VERTICES")
-    got2 = cuda_lib.estimate_decrease(gh, seeds, [], 3000, 1234, 2)
+    for k in ("IMIN_DISABLE_CTA_TIER", "IMIN_TIER0_VERTICES", "IMIN_TIER1_VERTICES",
+              "IMIN_CTA_EDGE_CAP"):
+        monkeypatch.delenv(k, raising=False)
+    got2, st2 = cuda_lib.estimate_decrease(gh, seeds, [], 3000, 1234, 2, stats=True)
     assert np.array_equal(got2, want)
+    assert st2["tier_samples"][3] == 3000  # default pipeline for n <= 2^18
+
+
+def test_warp_tiers_match_on_full_size_round(cuda_lib, monkeypatch, rmat17):
+    """The warp-tier pipeline (used for graphs above 2^18 vertices) on the bench graph, one
+    call at theta = 20,000, against the block tier's result (which the oracle pins below)."""
+    q = rmat17
+    gh = cuda_lib.load_graph(q.graph)
+    a = cuda_lib.estimate_decrease(gh, q.seeds, [], 20_000, q.key, 3)
+    monkeypatch.setenv("IMIN_DISABLE_CTA_TIER", "1")
+    b = cuda_lib.estimate_decrease(gh, q.seeds, [], 20_000, q.key, 3)
+    assert np.array_equal(a, b)
 
 
 def test_device_pointers_and_determinism(cuda_lib, tiny):
@@ -191,3 +213,16 @@ def test_full_size_advanced_greedy_sampled_rounds(cuda_lib, rmat17):
         d[q.seeds] = -1
         d[B[:i]] = -1
         assert int(np.argmax(d)) == int(B[i]), i
+
+
+@pytest.mark.parametrize("disable_block_tier", ["0", "1"])
+def test_many_seeds(cuda_lib, monkeypatch, disable_block_tier):
+    """A seed set too large for the shared-memory warp tier (4,000 seeds): the first tier that
+    can hold it takes the samples; counters still match the oracle."""
+    rp, col = W.chung_lu(5000, 40000, 2.1, seed=77)
+    g = W.Graph(5000, rp, col, W.wc_thresholds(col, 5000))
+    seeds = W.uniform_seeds(5000, 4000, seed=78)
+    monkeypatch.setenv("IMIN_DISABLE_CTA_TIER", disable_block_tier)
+    gh = cuda_lib.load_graph(g)
+    got = cuda_lib.estimate_decrease(gh, seeds, [], 500, 4242, 1)
+    assert np.array_equal(got, O.decrease(g, seeds, [], 500, 4242, 1))
