@@ -18,25 +18,22 @@
 
 using namespace imin;
 
-struct imin_graph {
-    int32_t n = 0;
-    int32_t m = 0;
-    int device = 0;
-    DeviceInfo dev;
-    int32_t* row_ptr = nullptr;
-    int32_t* col = nullptr;
-    uint4* thr4 = nullptr;
-};
+namespace imin {
+
+// Last error message of the calling thread, in a fixed buffer (recording it never allocates).
+thread_local char g_err[512] = "";
+
+int fail_msg(int code, const char* msg)
+{
+    std::snprintf(g_err, sizeof(g_err), "%s", msg);
+    return code;
+}
+
+}  // namespace imin
 
 namespace {
 
-thread_local std::string g_err;
-
-int fail(int code, const std::string& msg)
-{
-    g_err = msg;
-    return code;
-}
+int fail(int code, const std::string& msg) { return fail_msg(code, msg.c_str()); }
 
 int fail_cuda(cudaError_t e, const char* where)
 {
@@ -514,12 +511,12 @@ extern "C" {
 
 int imin_abi_version(void) { return IMIN_ABI_VERSION; }
 
-const char* imin_last_error(void) { return g_err.c_str(); }
+const char* imin_last_error(void) { return g_err; }
 
 int imin_load_graph(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t* col,
                     const uint32_t* thr, void* stream, imin_graph** out)
 {
-    g_err.clear();
+    g_err[0] = '\0';
     if (out == nullptr) return fail(IMIN_ERR_INVALID, "out is NULL");
     *out = nullptr;
     if (n <= 0) return fail(IMIN_ERR_INVALID, "n must be > 0");
@@ -616,7 +613,7 @@ int imin_estimate_decrease(const imin_graph* g, const int32_t* seeds, int32_t n_
                            const int32_t* blocked, int32_t n_blocked, uint32_t theta,
                            uint64_t key, uint32_t round, uint64_t* out_delta, void* stream)
 {
-    g_err.clear();
+    g_err[0] = '\0';
     return estimate_impl(g, seeds, n_seeds, blocked, n_blocked, theta, key, round, out_delta,
                          nullptr, stream);
 }
@@ -626,7 +623,7 @@ int imin_estimate_decrease_stats(const imin_graph* g, const int32_t* seeds, int3
                                  uint64_t key, uint32_t round, uint64_t* out_delta,
                                  imin_stats* stats, void* stream)
 {
-    g_err.clear();
+    g_err[0] = '\0';
     return estimate_impl(g, seeds, n_seeds, blocked, n_blocked, theta, key, round, out_delta,
                          stats, stream);
 }
@@ -635,7 +632,7 @@ int imin_advanced_greedy(const imin_graph* g, const int32_t* seeds, int32_t n_se
                          uint32_t theta, uint64_t key, int32_t* out_blockers, int32_t* out_count,
                          void* stream)
 {
-    g_err.clear();
+    g_err[0] = '\0';
     return greedy_impl(Driver::kAdvancedGreedy, g, seeds, n_seeds, b, theta, key, out_blockers,
                        out_count, stream);
 }
@@ -644,7 +641,7 @@ int imin_greedy_replace(const imin_graph* g, const int32_t* seeds, int32_t n_see
                         uint32_t theta, uint64_t key, int32_t* out_blockers, int32_t* out_count,
                         void* stream)
 {
-    g_err.clear();
+    g_err[0] = '\0';
     return greedy_impl(Driver::kGreedyReplace, g, seeds, n_seeds, b, theta, key, out_blockers,
                        out_count, stream);
 }

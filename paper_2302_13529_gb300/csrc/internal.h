@@ -9,7 +9,33 @@
 
 namespace imin {
 
-// Launch shape and capacities of the three sample tiers for one graph / seed-set size.
+struct DeviceInfo {
+    int device = 0;
+    int sms = 0;
+    uint64_t smem_optin = 0;
+};
+
+DeviceInfo device_info();
+
+// Record `msg` as the calling thread's last error (fixed buffer, no allocation); returns code.
+int fail_msg(int code, const char* msg);
+
+}  // namespace imin
+
+// A graph resident in device memory (the opaque handle of include/imin.h).
+struct imin_graph {
+    int32_t n = 0;
+    int32_t m = 0;
+    int device = 0;
+    imin::DeviceInfo dev;
+    int32_t* row_ptr = nullptr;  // [n+1]
+    int32_t* col = nullptr;      // [m] padded to a multiple of 4 (+4)
+    uint4* thr4 = nullptr;       // thresholds, same padding
+};
+
+namespace imin {
+
+// Launch shape and capacities of the sample tiers for one graph / seed-set size.
 struct TierPlan {
     TierCfg cfg[kTiers];
     uint32_t warps_per_block[kTiers];
@@ -19,14 +45,6 @@ struct TierPlan {
     bool use_cta = false;         // tier 3 replaces tiers 0 and 1
     CtaCfg cta{};
 };
-
-struct DeviceInfo {
-    int device = 0;
-    int sms = 0;
-    uint64_t smem_optin = 0;
-};
-
-DeviceInfo device_info();
 
 // Tier capacities for a graph with n vertices and m edges and a seed set of size ns.
 TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns);

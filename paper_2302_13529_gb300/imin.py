@@ -65,6 +65,7 @@ def lib():
         L.imin_estimate_decrease.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int32,
                                              ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
                                              P, P]
+        L.imin_estimate_decrease_noalloc.argtypes = L.imin_estimate_decrease.argtypes
         L.imin_estimate_decrease_stats.argtypes = L.imin_estimate_decrease.argtypes[:-1] + [
             ctypes.POINTER(Stats), P]
         for name in ("imin_advanced_greedy", "imin_greedy_replace"):
@@ -159,6 +160,20 @@ def estimate_decrease(gh: GraphHandle, seeds, blocked, theta, key, round_=0, out
         return out, st.as_dict()
     _check(lib().imin_estimate_decrease(gh.handle, s, ns, b, nb, int(theta), int(key),
                                         int(round_), o, _stream(stream)))
+    return out
+
+
+def estimate_decrease_noalloc(gh: GraphHandle, seeds, blocked, theta, key, round_=0, out=None,
+                              stream=None):
+    """imin_estimate_decrease_noalloc: the same counters as estimate_decrease, computed without
+    allocating memory (working memory comes from the library's static device array)."""
+    s, ks, ns = _ptr(seeds, np.int32)
+    b, kb, nb = _ptr(blocked if blocked is not None and len(blocked) else None, np.int32)
+    if out is None:
+        out = np.zeros(gh.n, dtype=np.uint64)
+    o, ko, _ = _ptr(out, np.uint64)
+    _check(lib().imin_estimate_decrease_noalloc(gh.handle, s, ns, b, nb, int(theta), int(key),
+                                                int(round_), o, _stream(stream)))
     return out
 
 
