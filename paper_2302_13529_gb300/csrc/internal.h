@@ -58,7 +58,7 @@ cudaError_t launch_sample_tier(int tier, const SampleParams& P, const TierPlan& 
                                uint8_t* scratch, cudaStream_t s, bool* launched);
 
 // Block-per-sample tier (graphs with n <= kCtaMaxVertices): layout, grid and shared memory.
-bool plan_cta_tier(const DeviceInfo& dev, int32_t n, CtaCfg* c, uint32_t* blocks, uint64_t* smem,
+bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint32_t* blocks, uint64_t* smem,
                    uint64_t* scratch_bytes);
 cudaError_t launch_cta_tier(const SampleParams& P, const CtaCfg& c, uint32_t blocks, uint64_t smem,
                             uint8_t* scratch, cudaStream_t s);

@@ -163,7 +163,7 @@ extern "C" int imin_estimate_decrease_noalloc(const imin_graph* g, const int32_t
     CtaCfg cfg{};
     uint32_t blocks = 0;
     uint64_t smem = 0, slot_total = 0;
-    if (!plan_cta_tier(g->dev, g->n, &cfg, &blocks, &smem, &slot_total))
+    if (!plan_cta_tier(g->dev, g->n, g->m, &cfg, &blocks, &smem, &slot_total))
         return fail_msg(IMIN_ERR_INTERNAL, "the block-per-sample kernel cannot be configured");
     if (off_slots + cfg.slot_bytes > kNoAllocBytes)
         return fail_msg(IMIN_ERR_INVALID, "imin_estimate_decrease_noalloc: request exceeds the static scratch");

@@ -144,7 +144,7 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns)
     uint64_t t2_budget = static_cast<uint64_t>(env_u32("IMIN_TIER2_MIB", 4096)) << 20;
 
     // tier 3: block per sample with a shared-memory visited bitmap, whenever n allows
-    if (allow_cta && plan_cta_tier(dev, n, &p.cta, &p.blocks[kTierCta], &p.smem_bytes[kTierCta],
+    if (allow_cta && plan_cta_tier(dev, n, m, &p.cta, &p.blocks[kTierCta], &p.smem_bytes[kTierCta],
                                    &p.scratch_bytes[kTierCta])) {
         p.use_cta = true;
         p.warps_per_block[kTierCta] = 4;

@@ -1,0 +1,376 @@
+// sample_cta.cuh -- the block-per-sample routine of Alg. 2 for graphs whose visited bitmap fits
+// in shared memory (n <= 2^18), shared by the single-query kernel (sample_cta.cu) and the
+// batched multi-query kernel (batch.cu).
+//
+// One 128-thread block owns one sampled graph at a time (persistent over the samples of the
+// call through an atomic cursor):
+//   * visited set: an n-bit bitmap in shared memory; discovering a vertex is one shared-memory
+//     atomicOr, so no cascade size ever overflows the visited structure;
+//   * BFS level by level, 256 frontier vertices per block-wide scan: their out-edges are
+//     flattened into 4-edge groups; each thread takes 2 consecutive groups (one binary search
+//     for the owner row, two independent Philox4x32-10 chains), loads each group's 4 thresholds
+//     with one 16-byte load and decides them with one Philox call;
+//   * live edges (a few percent of the examined ones) are staged per warp and then visited by
+//     the whole warp: target load, visited test-and-set, and one shared atomic per warp to
+//     hand out local ids (ballot + popcount), so the rare live edges do not serialise the warp;
+//   * per-vertex arrays indexed by local id (BFS discovery order) -- global id, BFS parent,
+//     immediate dominator -- live in a per-block slot of global memory that is written once
+//     per discovery and read back densely, so it streams through L2;
+//   * live edges to already-visited vertices ("non-tree" edges) are rare; their targets are
+//     resolved from global to local ids afterwards through a small hash built in the (then
+//     cleared) bitmap space, in chunks when there are many;
+//   * dominators, subtree sizes and the counter update follow the same scheme as the warp
+//     tiers (imin_dev.cuh): iterated NCA folding over non-tree edges plus each target's BFS
+//     parent, a deepest-level-first subtree sweep, and 64-bit atomics into Delta.
+// A sample that exceeds the non-tree edge capacity or the level capacity is abandoned and
+// handed to the whole-graph warp tier (tier 2).
+#pragma once
+
+#include "imin_dev.cuh"
+
+namespace imin {
+namespace cta {
+
+constexpr uint32_t kCtaThreads = 128;
+constexpr uint32_t kCtaWarps = kCtaThreads / 32;
+constexpr uint32_t kVpt = 2;                        // frontier vertices per thread per chunk
+constexpr uint32_t kChunk = kCtaThreads * kVpt;     // frontier vertices per chunk
+constexpr uint32_t kGpt = 2;                        // consecutive 4-edge groups per thread
+constexpr uint32_t kStage = 32 * 4;                 // live edges staged per warp and group slot
+constexpr uint32_t kCtaLevels = 512;
+
+struct CtaShared {
+    uint32_t incl[kChunk];  // inclusive group count of the chunk's vertices
+    int32_t beg[kChunk];    // their edge ranges
+    int32_t end[kChunk];
+    uint32_t lvl[kCtaLevels + 1];
+    uint2 stage[kCtaWarps][kStage];  // (local id of the source, edge id)
+    uint32_t wsum[kCtaWarps];
+    uint32_t item, nR, nE, flag;
+};
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t tid, CtaShared& sh,
+                                                    uint32_t* total)
+{
+    const uint32_t lane = tid & 31, wid = tid >> 5;
+    const uint32_t incl = warp_incl_scan(x, lane);
+    if (lane == 31) sh.wsum[wid] = incl;
+    __syncthreads();
+    uint32_t off = 0, tot = 0;
+#pragma unroll
+    for (uint32_t w = 0; w < kCtaWarps; ++w) {
+        const uint32_t s = sh.wsum[w];
+        if (w < wid) off += s;
+        tot += s;
+    }
+    *total = tot;
+    return incl - x + off;
+}
+
+// Find-or-insert of a global id in the resolution hash (keys then values, h slots each).
+__device__ __forceinline__ uint32_t res_slot(uint32_t* keys, uint32_t hmask, uint32_t hshift,
+                                             uint32_t v, bool insert)
+{
+    uint32_t slot = (v * 0x9E3779B1u) >> hshift;
+    for (uint32_t probe = 0; probe <= hmask; ++probe) {
+        const uint32_t k = *reinterpret_cast<volatile uint32_t*>(keys + slot);
+        if (k == v) return slot;
+        if (k == kEmpty) {
+            if (!insert) return kEmpty;
+            const uint32_t prev = atomicCAS(keys + slot, kEmpty, v);
+            if (prev == kEmpty || prev == v) return slot;
+        }
+        slot = (slot + 1) & hmask;
+    }
+    return kEmpty;
+}
+
+struct Slot {
+    int32_t* gid;
+    uint32_t* par;   // BFS parent; reused for subtree sizes after the dominator passes
+    uint32_t* idom;
+    uint2* edges;
+};
+
+// Visit the staged live edges of one warp: test-and-set the visited bit of each target; a new
+// vertex gets the next local id (one shared atomic per warp), an old one yields a non-tree edge.
+__device__ __forceinline__ void visit_staged(const SampleParams& P, const CtaCfg& C, uint32_t* bm,
+                                             CtaShared& sh, const Slot& S, const uint2* stage,
+                                             uint32_t count, uint32_t lane,
+                                             unsigned long long& lv)
+{
+    for (uint32_t s0 = 0; s0 < count; s0 += 32) {
+        const bool act = s0 + lane < count;
+        bool disc = false, nt = false;
+        uint32_t ul = 0, v = 0;
+        if (act) {
+            const uint2 c = stage[s0 + lane];
+            ul = c.x;
+            v = static_cast<uint32_t>(__ldg(P.g.col + c.y));
+            if (!excluded(P.excl, v)) {
+                ++lv;
+                const uint32_t bit = 1u << (v & 31);
+                disc = (atomicOr(bm + (v >> 5), bit) & bit) == 0;
+                nt = !disc;
+            }
+        }
+        const uint32_t dm = __ballot_sync(kFull, disc);
+        if (dm) {
+            uint32_t b = 0;
+            const uint32_t leader = __ffs(dm) - 1;
+            if (lane == leader) b = atomicAdd(&sh.nR, __popc(dm));
+            b = __shfl_sync(kFull, b, leader);
+            if (disc) {
+                const uint32_t lid = b + __popc(dm & lanemask_lt());
+                if (lid < C.rcap) {
+                    S.gid[lid] = static_cast<int32_t>(v);
+                    S.par[lid] = ul;
+                    S.idom[lid] = ul;
+                } else {
+                    sh.flag = 1;
+                }
+            }
+        }
+        const uint32_t nm = __ballot_sync(kFull, nt);
+        if (nm) {
+            uint32_t b = 0;
+            const uint32_t leader = __ffs(nm) - 1;
+            if (lane == leader) b = atomicAdd(&sh.nE, __popc(nm));
+            b = __shfl_sync(kFull, b, leader);
+            if (nt) {
+                const uint32_t pe = b + __popc(nm & lanemask_lt());
+                if (pe < C.ecap) S.edges[pe] = make_uint2(ul, v);
+                else sh.flag = 1;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCfg& C, uint32_t* bm,
+                                              CtaShared& sh, const Slot& S, uint32_t j,
+                                              uint32_t tid, SampleCounters& sc,
+                                              unsigned long long& examined, unsigned long long& live)
+{
+    const uint32_t ns = P.ns;
+    const uint32_t lane = tid & 31, wid = tid >> 5;
+    for (uint32_t i = tid; i < ns; i += kCtaThreads) {
+        S.gid[1 + i] = P.seeds[i];
+        S.idom[1 + i] = 0;
+        S.par[1 + i] = 0;
+    }
+    if (tid == 0) {
+        S.idom[0] = 0;
+        S.par[0] = 0;
+        sh.lvl[0] = 1;
+        sh.lvl[1] = 1 + ns;
+        sh.nR = 1 + ns;
+        sh.nE = 0;
+        sh.flag = 0;
+    }
+    __syncthreads();
+
+    uint32_t lb = 1, le = 1 + ns, nlev = 1;
+    unsigned long long ex = 0, lv = 0;
+    bool over = false;
+    while (lb < le) {
+        for (uint32_t base = lb; base < le; base += kChunk) {
+            // ---- the chunk's vertices (kVpt consecutive per thread) and their 4-edge groups
+            int32_t beg[kVpt], end[kVpt];
+            uint32_t ng[kVpt], sum = 0;
+#pragma unroll
+            for (uint32_t k = 0; k < kVpt; ++k) {
+                const uint32_t idx = base + tid * kVpt + k;
+                beg[k] = 0;
+                end[k] = 0;
+                if (idx < le) {
+                    const int32_t u = S.gid[idx];
+                    beg[k] = __ldg(P.g.row_ptr + u);
+                    end[k] = __ldg(P.g.row_ptr + u + 1);
+                }
+                ex += static_cast<uint32_t>(end[k] - beg[k]);
+                ng[k] = end[k] > beg[k]
+                            ? (static_cast<uint32_t>(end[k] - 1) >> 2) - (static_cast<uint32_t>(beg[k]) >> 2) + 1
+                            : 0u;
+                sum += ng[k];
+            }
+            uint32_t total;
+            uint32_t run = block_excl_scan(sum, tid, sh, &total);
+#pragma unroll
+            for (uint32_t k = 0; k < kVpt; ++k) {
+                run += ng[k];
+                sh.incl[tid * kVpt + k] = run;
+                sh.beg[tid * kVpt + k] = beg[k];
+                sh.end[tid * kVpt + k] = end[k];
+            }
+            __syncthreads();
+
+            // ---- groups: kGpt consecutive per thread, one owner search per thread
+            for (uint32_t t0 = 0; t0 < total; t0 += kCtaThreads * kGpt) {
+                const uint32_t tb = t0 + tid * kGpt;
+                uint32_t p = 0;
+                if (tb < total) {
+#pragma unroll
+                    for (uint32_t step = kChunk / 2; step >= 1; step >>= 1)
+                        if (sh.incl[p + step - 1] <= tb) p += step;
+                }
+                uint32_t q[kGpt], ul[kGpt];
+                int32_t ob[kGpt], oe[kGpt];
+                uint4 th[kGpt];
+#pragma unroll
+                for (uint32_t k = 0; k < kGpt; ++k) {
+                    const uint32_t t = tb + k;
+                    ob[k] = 0;
+                    oe[k] = 0;
+                    q[k] = 0;
+                    ul[k] = 0;
+                    if (t < total) {
+                        while (sh.incl[p] <= t) ++p;  // next non-empty row (t < total keeps p in range)
+                        ob[k] = sh.beg[p];
+                        oe[k] = sh.end[p];
+                        const uint32_t first = p ? sh.incl[p - 1] : 0u;
+                        q[k] = (static_cast<uint32_t>(ob[k]) >> 2) + (t - first);
+                        ul[k] = base + p;
+                        th[k] = __ldg(P.g.thr4 + q[k]);
+                    }
+                }
+#pragma unroll
+                for (uint32_t k = 0; k < kGpt; ++k) {
+                    uint32_t m = 0;
+                    if (oe[k] > ob[k]) {
+                        const uint4 r = philox4x32_10(make_uint4(q[k], j, P.round, 0u), P.key_lo, P.key_hi);
+                        const int32_t e0 = static_cast<int32_t>(q[k] << 2);
+                        m |= (e0 + 0 >= ob[k] && e0 + 0 < oe[k] && r.x <= th[k].x) ? 1u : 0u;
+                        m |= (e0 + 1 >= ob[k] && e0 + 1 < oe[k] && r.y <= th[k].y) ? 2u : 0u;
+                        m |= (e0 + 2 >= ob[k] && e0 + 2 < oe[k] && r.z <= th[k].z) ? 4u : 0u;
+                        m |= (e0 + 3 >= ob[k] && e0 + 3 < oe[k] && r.w <= th[k].w) ? 8u : 0u;
+                    }
+                    // stage this lane's live edges of group slot k, then visit them as a warp
+                    const uint32_t nc = __popc(m);
+                    const uint32_t cincl = warp_incl_scan(nc, lane);
+                    const uint32_t ctot = __shfl_sync(kFull, cincl, 31);
+                    if (ctot == 0) continue;
+                    uint32_t w = cincl - nc;
+                    while (m) {
+                        const uint32_t i = __ffs(m) - 1;
+                        m &= m - 1;
+                        sh.stage[wid][w++] = make_uint2(ul[k], (q[k] << 2) + i);
+                    }
+                    __syncwarp();
+                    visit_staged(P, C, bm, sh, S, sh.stage[wid], ctot, lane, lv);
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+        }
+        const uint32_t nR = *reinterpret_cast<volatile uint32_t*>(&sh.nR);
+        if (*reinterpret_cast<volatile uint32_t*>(&sh.flag)) { over = true; break; }
+        if (nR > le) {
+            if (nlev + 1 > kCtaLevels) { over = true; break; }
+            if (tid == 0) sh.lvl[nlev + 1] = nR;
+            ++nlev;
+        }
+        lb = le;
+        le = nR;
+    }
+    __syncthreads();
+
+    if (over) {
+        for (uint32_t i = tid; i < C.bm_words; i += kCtaThreads) bm[i] = 0;
+        __syncthreads();
+        return kSampleOverflow;
+    }
+    examined += ex;
+    live += lv;
+    const uint32_t nR = sh.nR, nE = sh.nE;
+    bool broken = false;
+
+    // clear the visited bits (seeds were never marked)
+    for (uint32_t i = 1 + ns + tid; i < nR; i += kCtaThreads) bm[S.gid[i] >> 5] = 0;
+    __syncthreads();
+
+    // non-tree edge targets: global id -> local id through a hash in the bitmap space, in
+    // chunks of at most half the hash's slots
+    if (nE > 0) {
+        uint32_t* keys = bm;
+        uint32_t* vals = bm + C.res_slots;
+        const uint32_t hmask = C.res_slots - 1;
+        for (uint32_t c0 = 0; c0 < nE; c0 += C.res_slots / 2) {
+            const uint32_t c1 = min(nE, c0 + C.res_slots / 2);
+            for (uint32_t i = tid; i < C.res_slots; i += kCtaThreads) keys[i] = kEmpty;
+            __syncthreads();
+            for (uint32_t k = c0 + tid; k < c1; k += kCtaThreads)
+                res_slot(keys, hmask, C.res_shift, S.edges[k].y, true);
+            __syncthreads();
+            for (uint32_t i = 1 + ns + tid; i < nR; i += kCtaThreads) {
+                const uint32_t s = res_slot(keys, hmask, C.res_shift, static_cast<uint32_t>(S.gid[i]), false);
+                if (s != kEmpty) vals[s] = i;
+            }
+            __syncthreads();
+            for (uint32_t k = c0 + tid; k < c1; k += kCtaThreads) {
+                const uint32_t s = res_slot(keys, hmask, C.res_shift, S.edges[k].y, false);
+                if (s == kEmpty) broken = true;  // every target was reached: cannot happen
+                else S.edges[k].y = vals[s];
+            }
+            __syncthreads();
+        }
+        for (uint32_t i = tid; i < 2 * C.res_slots; i += kCtaThreads) bm[i] = 0;
+        broken = __syncthreads_or(broken);
+        if (broken) return kSampleError;
+    }
+
+    // immediate dominators: fold NCA(idom(v), p, parent(v)) over the non-tree edges
+    uint32_t passes = 0;
+    if (nE > 0) {
+        for (;;) {
+            int changed = 0;
+            for (uint32_t k = tid; k < nE; k += kCtaThreads) {
+                const uint2 e = S.edges[k];
+                uint32_t a = __ldcg(S.idom + e.y), b = e.x;
+                for (uint32_t g = 0; a != b; ++g) {
+                    if (g > 2 * nR) { broken = true; a = 0; break; }
+                    if (a > b) a = __ldcg(S.idom + a);
+                    else b = __ldcg(S.idom + b);
+                }
+                b = S.par[e.y];
+                for (uint32_t g = 0; a != b; ++g) {
+                    if (g > 2 * nR) { broken = true; a = 0; break; }
+                    if (a > b) a = __ldcg(S.idom + a);
+                    else b = __ldcg(S.idom + b);
+                }
+                if (!broken && a < __ldcg(S.idom + e.y)) {
+                    const uint32_t old = atomicMin(S.idom + e.y, a);
+                    changed |= a < old;
+                }
+            }
+            ++passes;
+            broken = __syncthreads_or(broken);
+            if (broken || !__syncthreads_or(changed)) break;
+            if (passes > nR + 1) { broken = true; break; }
+        }
+    }
+
+    // subtree sizes, deepest level first (c reuses the parent array)
+    uint32_t* c = S.par;
+    for (uint32_t i = tid; i < nR; i += kCtaThreads) c[i] = 1;
+    __syncthreads();
+    for (uint32_t d = nlev - 1; d >= 1; --d) {
+        const uint32_t b0 = sh.lvl[d], b1 = sh.lvl[d + 1];
+        for (uint32_t i = b0 + tid; i < b1; i += kCtaThreads)
+            atomicAdd(c + __ldcg(S.idom + i), __ldcg(c + i));
+        __syncthreads();
+    }
+    for (uint32_t i = 1 + ns + tid; i < nR; i += kCtaThreads)
+        atomicAdd(P.delta + S.gid[i], static_cast<unsigned long long>(__ldcg(c + i)));
+    __syncthreads();
+
+    if (tid == 0) {
+        sc.reached += nR - 1;
+        sc.nontree += nE;
+        sc.passes += passes;
+        sc.done += 1;
+    }
+    return broken ? kSampleError : kSampleDone;
+}
+
+}  // namespace cta
+}  // namespace imin
