@@ -48,6 +48,9 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target CPU time of the oracle baseline sample")
+    p.add_argument("--workload", choices=("rmat17", "batch256"), default="rmat17",
+                   help="rmat17: one AdvancedGreedy query on R-MAT 2^17 (the headline line); "
+                        "batch256: 256 Chung-Lu/TR queries, batched vs one query per launch")
     return p.parse_args(argv)
 
 
@@ -237,6 +240,65 @@ def config_of(q):
             "l2": "flushed between steps (512 MiB write outside the step events)"}
 
 
+def run_batch(args, rank, world, dist):
+    """256 independent AdvancedGreedy queries (Chung-Lu, n log-uniform in [1e3, 2e5], mean degree
+    U[5,20], TR probabilities, |S| U[5,100], b=20, theta=2e4): one batched call (a step) vs the
+    same queries one imin_advanced_greedy call at a time; the results must be identical."""
+    import numpy as np
+    import torch
+    from paper_2302_13529_gb300 import build, imin, workloads as W
+
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.perf_counter()
+    qs = W.batch_queries(256)
+    gen_s = time.perf_counter() - t0
+    hs = [imin.load_graph(q.graph) for q in qs]
+    items = [(h, q.seeds, q.b, q.theta, q.key + rank) for h, q in zip(hs, qs)]
+    samples = sum(q.b * q.theta for q in qs)  # every query runs b rounds (n - |S| >= b here)
+    for _ in range(max(args.warmup, 3) if args.warmup else 1):
+        imin.batch_advanced_greedy(items)
+    torch.cuda.synchronize()
+    imin.profile_read(reset=True)
+    imin.profile_enable(True)
+    launches0 = imin.launch_count()
+    times = []
+    res = None
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = imin.batch_advanced_greedy(items)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+    launches = imin.launch_count() - launches0
+    imin.profile_enable(False)
+    prof = imin.profile_read(reset=True)
+    st = imin.last_stats()
+    t = time.perf_counter()
+    plain = [imin.advanced_greedy(*it) for it in items]
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t
+    same = all(np.array_equal(a, b) for a, b in zip(res, plain))
+    batched_s = sum(times) / len(times)
+    line = {"metric": METRIC, "value": samples / batched_s, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * batched_s,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "uint32",
+            "data": "synthetic",
+            "config": {"workload": "batch256-chunglu-tr-advanced-greedy", "queries": len(qs),
+                       "b": 20, "theta": 20000, "samples_per_step": samples,
+                       "total_edges": int(sum(q.graph.m for q in qs)),
+                       "generation_s": round(gen_s, 1)},
+            "one_query_per_launch": {"value": samples / plain_s, "unit": "samples/s",
+                                     "seconds": plain_s},
+            "batched_over_plain": plain_s / batched_s, "bit_exact_vs_plain": same,
+            "gpu_launches": launches,
+            "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
+            "work": {"reached_per_sample": st["reached"] / max(st["samples"], 1),
+                     "examined_edges_per_sample": st["examined_edges"] / max(st["samples"], 1)}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     rank, world, local_rank = dist_env()
@@ -253,6 +315,9 @@ def main(argv=None):
             tdist.init_process_group("gloo")
         dist = tdist
 
+    if args.workload == "batch256":
+        run_batch(args, rank, world, dist)
+        return
     q = W.rmat17_query()
     if args.impl == "reference":
         run_reference(args, q, rank)

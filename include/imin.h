@@ -134,6 +134,32 @@ int imin_estimate_decrease_noalloc(const imin_graph* g, const int32_t* seeds, in
                                    uint64_t key, uint32_t round, uint64_t* out_delta,
                                    void* stream);
 
+/* ---- batched drivers ----------------------------------------------------------------------
+ * Many independent queries -- each with its own loaded graph, seed set, budget, theta and key --
+ * advanced together: every greedy round is one launch over the sampled graphs of all queries
+ * still active, load-balanced over the whole GPU, followed by one selection launch with a block
+ * per query. Each query's result (blockers and count) is identical to what
+ * imin_advanced_greedy / imin_greedy_replace return for it alone (same random streams, same
+ * round numbering, same tie rule). Graphs must all live on the current device. When a graph has
+ * more than 2^18 vertices the batch runs its queries one at a time. */
+typedef struct imin_query {
+    const imin_graph* graph;  /* in: loaded graph */
+    const int32_t* seeds;     /* in: n_seeds distinct vertex ids (host or device) */
+    int32_t n_seeds;
+    int32_t b;                /* in: budget */
+    uint32_t theta;           /* in: sampled graphs per round */
+    uint64_t key;             /* in: random-stream key */
+    int32_t* out_blockers;    /* out: int32[b] (host or device), blockers in the driver's order */
+    int32_t out_count;        /* out: number of blockers written */
+} imin_query;
+
+/* Alg. 3 for every query of `queries` (n_queries >= 0). Synchronizes `stream`. Errors as for
+ * imin_advanced_greedy; on error no out_count is meaningful. */
+int imin_batch_advanced_greedy(imin_query* queries, int32_t n_queries, void* stream);
+
+/* Alg. 4 for every query of `queries`; GreedyReplace's phase-2 early stop is per query. */
+int imin_batch_greedy_replace(imin_query* queries, int32_t n_queries, void* stream);
+
 /* Work counters of one Alg. 2 call, for throughput accounting (not part of the method). */
 typedef struct imin_stats {
     uint64_t samples;        /* sampled graphs processed (theta) */

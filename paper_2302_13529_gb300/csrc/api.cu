@@ -5,6 +5,7 @@
 // (phase-1 calls with selection over CB, then replacement calls with an on-device stop flag).
 // All launches of one entry point go to the caller's stream; per-call buffers come from the
 // stream-ordered allocator and are released on the same stream.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -505,6 +506,217 @@ int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t
     return IMIN_OK;
 }
 
+
+// ---- batched drivers ------------------------------------------------------------------------
+
+int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (nq < 0 || (nq > 0 && qs == nullptr)) return fail(IMIN_ERR_INVALID, "queries array is NULL");
+    if (nq == 0) return IMIN_OK;
+    const bool gr = which == Driver::kGreedyReplace;
+    // validation, host copies of the seed sets
+    std::vector<std::vector<int32_t>> hseeds(nq);
+    int32_t max_n = 0, max_m = 0;
+    uint32_t max_ns = 0;
+    bool fits = true;
+    for (int32_t i = 0; i < nq; ++i) {
+        imin_query& Q = qs[i];
+        Q.out_count = 0;
+        std::vector<uint8_t> mark;
+        int rc = common_checks(Q.graph, Q.seeds, Q.n_seeds, Q.theta, s, hseeds[i], mark);
+        if (rc) return rc;
+        if (Q.b < 0) return fail(IMIN_ERR_INVALID, "b must be >= 0");
+        if (Q.b > 0 && Q.out_blockers == nullptr) return fail(IMIN_ERR_INVALID, "out_blockers is NULL");
+        if (Q.graph->device != qs[0].graph->device)
+            return fail(IMIN_ERR_INVALID, "all graphs of a batch must live on one device");
+        max_n = std::max(max_n, Q.graph->n);
+        max_m = std::max(max_m, Q.graph->m);
+        max_ns = std::max<uint32_t>(max_ns, static_cast<uint32_t>(Q.n_seeds));
+        fits = fits && Q.graph->n <= kCtaMaxVertices;
+    }
+    if (!fits) {
+        // graphs above the block tier's size run one query at a time
+        for (int32_t i = 0; i < nq; ++i) {
+            imin_query& Q = qs[i];
+            int rc = greedy_impl(which, Q.graph, Q.seeds, Q.n_seeds, Q.b, Q.theta, Q.key,
+                                 Q.out_blockers, &Q.out_count, stream);
+            if (rc) return rc;
+        }
+        return IMIN_OK;
+    }
+    const imin_graph* g0 = qs[0].graph;
+    CtaCfg cfg{};
+    uint32_t cta_blocks = 0;
+    uint64_t cta_smem = 0, cta_bytes = 0;
+    if (!plan_batch_cta(g0->dev, max_n, max_m, &cfg, &cta_blocks, &cta_smem, &cta_bytes))
+        return fail(IMIN_ERR_INTERNAL, "the batched block-per-sample kernel cannot be configured");
+    const TierPlan wp = plan_tiers(g0->dev, max_n, max_m, max_ns);
+
+    // per-query device buffers, packed into one allocation
+    struct Off { uint64_t excl, cb, delta, flags; };
+    std::vector<Off> off(nq);
+    std::vector<uint64_t> seed_off(nq + 1, 0), blk_off(nq + 1, 0);
+    uint64_t total = 0;
+    auto take = [&](uint64_t bytes) { const uint64_t o = total; total = align16(total + bytes); return o; };
+    uint64_t sum_theta = 0;
+    for (int32_t i = 0; i < nq; ++i) {
+        const imin_query& Q = qs[i];
+        const uint64_t words = (Q.graph->n + 31) / 32;
+        off[i].excl = take(4ull * words);
+        off[i].cb = take(gr ? 4ull * words : 0);
+        off[i].delta = take(8ull * Q.graph->n);
+        off[i].flags = take(8);
+        seed_off[i + 1] = seed_off[i] + static_cast<uint64_t>(Q.n_seeds);
+        blk_off[i + 1] = blk_off[i] + static_cast<uint64_t>(Q.b);
+        sum_theta += Q.theta;
+    }
+    Arena arena(s);
+    uint8_t* buf = nullptr;
+    BatchQuery* dq = nullptr;
+    uint8_t* cta_scratch = nullptr;
+    uint8_t* whole_scratch = nullptr;
+    unsigned long long* stats = nullptr;
+    uint2* over = nullptr;
+    uint32_t* cb_counts = nullptr;
+    int32_t* dseeds = nullptr;
+    int32_t* dblk = nullptr;
+    IMIN_CUDA(arena.alloc(&buf, total));
+    IMIN_CUDA(arena.alloc(&dseeds, seed_off[nq]));
+    IMIN_CUDA(arena.alloc(&dblk, std::max<uint64_t>(blk_off[nq], 1)));
+    IMIN_CUDA(arena.alloc(&dq, nq));
+    IMIN_CUDA(arena.alloc(&cta_scratch, cta_bytes));
+    IMIN_CUDA(arena.alloc(&whole_scratch, wp.scratch_bytes[kTierWhole]));
+    IMIN_CUDA(arena.alloc(&stats, kStCount));
+    IMIN_CUDA(arena.alloc(&over, sum_theta));
+    IMIN_CUDA(arena.alloc(&cb_counts, nq));
+    IMIN_CUDA(cudaMemsetAsync(buf, 0, total, s));
+    IMIN_CUDA(cudaMemsetAsync(whole_scratch, 0xFF, wp.scratch_bytes[kTierWhole], s));
+    IMIN_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * kStCount, s));
+    IMIN_CUDA(cudaMemsetAsync(cb_counts, 0, sizeof(uint32_t) * nq, s));
+    std::vector<int32_t> hseed_all(seed_off[nq]);
+    for (int32_t i = 0; i < nq; ++i)
+        std::memcpy(hseed_all.data() + seed_off[i], hseeds[i].data(), 4ull * hseeds[i].size());
+    IMIN_CUDA(cudaMemcpyAsync(dseeds, hseed_all.data(), 4ull * seed_off[nq], cudaMemcpyHostToDevice, s));
+    for (int32_t i = 0; i < nq; ++i) {
+        IMIN_CUDA(launch_build_excl(reinterpret_cast<uint32_t*>(buf + off[i].excl), dseeds + seed_off[i],
+                                    qs[i].n_seeds, s));
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    std::vector<int32_t> count(nq);
+    if (gr) {
+        for (int32_t i = 0; i < nq; ++i) {
+            IMIN_CUDA(launch_build_cb(dev_graph(qs[i].graph), dseeds + seed_off[i],
+                                      qs[i].n_seeds, reinterpret_cast<uint32_t*>(buf + off[i].excl),
+                                      reinterpret_cast<uint32_t*>(buf + off[i].cb), cb_counts + i, s));
+            g_launches.fetch_add(2, std::memory_order_relaxed);
+        }
+        std::vector<uint32_t> hcb(nq);
+        IMIN_CUDA(cudaMemcpyAsync(hcb.data(), cb_counts, sizeof(uint32_t) * nq, cudaMemcpyDeviceToHost, s));
+        IMIN_CUDA(cudaStreamSynchronize(s));
+        for (int32_t i = 0; i < nq; ++i) count[i] = std::min<int32_t>(qs[i].b, static_cast<int32_t>(hcb[i]));
+    } else {
+        for (int32_t i = 0; i < nq; ++i) count[i] = std::min<int32_t>(qs[i].b, qs[i].graph->n - qs[i].n_seeds);
+    }
+    std::vector<BatchQuery> hq(nq);
+    int32_t steps = 0;
+    for (int32_t i = 0; i < nq; ++i) {
+        const imin_query& Q = qs[i];
+        BatchQuery& d = hq[i];
+        d.g = dev_graph(Q.graph);
+        d.seeds = dseeds + seed_off[i];
+        d.ns = static_cast<uint32_t>(Q.n_seeds);
+        d.excl = reinterpret_cast<uint32_t*>(buf + off[i].excl);
+        d.cb = gr ? reinterpret_cast<uint32_t*>(buf + off[i].cb) : nullptr;
+        d.key_lo = static_cast<uint32_t>(Q.key);
+        d.key_hi = static_cast<uint32_t>(Q.key >> 32);
+        d.theta = Q.theta;
+        d.delta = reinterpret_cast<unsigned long long*>(buf + off[i].delta);
+        d.blockers = dblk + blk_off[i];
+        d.count = count[i];
+        d.flags = reinterpret_cast<int32_t*>(buf + off[i].flags);
+        steps = std::max(steps, gr ? 2 * count[i] : count[i]);
+    }
+    IMIN_CUDA(cudaMemcpyAsync(dq, hq.data(), sizeof(BatchQuery) * nq, cudaMemcpyHostToDevice, s));
+
+    // per-step item prefixes: an inactive query contributes no items
+    const uint32_t chunk = static_cast<uint32_t>(std::max<uint64_t>(
+        1, std::min<uint64_t>(64, sum_theta / (static_cast<uint64_t>(cta_blocks) * 16 + 1))));
+    std::vector<unsigned long long> hprefix(static_cast<size_t>(steps) * (nq + 1), 0);
+    for (int32_t c = 0; c < steps; ++c) {
+        unsigned long long* pr = hprefix.data() + static_cast<size_t>(c) * (nq + 1);
+        for (int32_t i = 0; i < nq; ++i) {
+            const bool act = gr ? c < 2 * count[i] : c < count[i];
+            pr[i + 1] = pr[i] + (act ? (qs[i].theta + chunk - 1) / chunk : 0);
+        }
+    }
+    unsigned long long* dprefix = nullptr;
+    BatchCtl* ctl = nullptr;
+    IMIN_CUDA(arena.alloc(&dprefix, std::max<uint64_t>(hprefix.size(), 1)));
+    IMIN_CUDA(arena.alloc(&ctl, std::max(steps, 1)));
+    if (!hprefix.empty())
+        IMIN_CUDA(cudaMemcpyAsync(dprefix, hprefix.data(), sizeof(unsigned long long) * hprefix.size(),
+                                  cudaMemcpyHostToDevice, s));
+    IMIN_CUDA(cudaMemsetAsync(ctl, 0, sizeof(BatchCtl) * std::max(steps, 1), s));
+
+    CallTimer T(s);
+    for (int32_t c = 0; c < steps; ++c) {
+        BatchStep B{};
+        B.q = dq;
+        B.nq = static_cast<uint32_t>(nq);
+        B.prefix = dprefix + static_cast<size_t>(c) * (nq + 1);
+        B.chunk = chunk;
+        B.step = static_cast<uint32_t>(c);
+        B.gr = gr ? 1 : 0;
+        B.ctl = ctl + c;
+        B.over = over;
+        B.over_cap = static_cast<uint32_t>(std::min<uint64_t>(sum_theta, 0xFFFFFFFFull));
+        B.stats = stats;
+        if (gr) {
+            IMIN_CUDA(T.run(kKindOther, [&](bool* l) { *l = true; return launch_batch_unblock(B, s); }));
+        }
+        IMIN_CUDA(T.run(kKindCta, [&](bool* l) {
+            *l = true;
+            return launch_batch_cta(B, cfg, cta_blocks, cta_smem, cta_scratch, s);
+        }));
+        IMIN_CUDA(T.run(kKindTier2, [&](bool* l) {
+            *l = true;
+            return launch_batch_whole(B, wp.cfg[kTierWhole], wp.blocks[kTierWhole], whole_scratch, s);
+        }));
+        IMIN_CUDA(T.run(kKindSelect, [&](bool* l) { *l = true; return launch_batch_select(B, s); }));
+    }
+
+    std::vector<BatchCtl> hctl(std::max(steps, 1));
+    std::vector<int32_t> hblk(std::max<uint64_t>(blk_off[nq], 1));
+    unsigned long long hstats[kStCount];
+    IMIN_CUDA(cudaMemcpyAsync(hctl.data(), ctl, sizeof(BatchCtl) * hctl.size(), cudaMemcpyDeviceToHost, s));
+    IMIN_CUDA(cudaMemcpyAsync(hblk.data(), dblk, 4ull * blk_off[nq], cudaMemcpyDeviceToHost, s));
+    IMIN_CUDA(cudaMemcpyAsync(hstats, stats, sizeof(hstats), cudaMemcpyDeviceToHost, s));
+    IMIN_CUDA(cudaStreamSynchronize(s));
+    T.collect();
+    uint32_t err = 0;
+    for (int32_t c = 0; c < steps; ++c) err |= hctl[c].error;
+    if (err & kErrInternal) return fail(IMIN_ERR_INTERNAL, "dominator iteration did not converge");
+    if (err & kErrCapacity)
+        return fail(IMIN_ERR_CAPACITY, "a sampled cascade exceeded the largest tier's capacity");
+    record_stats(hstats);
+    for (int32_t i = 0; i < nq; ++i) {
+        imin_query& Q = qs[i];
+        const int32_t* src = hblk.data() + blk_off[i];
+        if (count[i] > 0) {
+            if (is_device_ptr(Q.out_blockers)) {
+                IMIN_CUDA(cudaMemcpyAsync(Q.out_blockers, dblk + blk_off[i], 4ull * count[i],
+                                          cudaMemcpyDeviceToDevice, s));
+            } else {
+                std::memcpy(Q.out_blockers, src, 4ull * count[i]);
+            }
+        }
+        Q.out_count = count[i];
+    }
+    IMIN_CUDA(cudaStreamSynchronize(s));
+    return IMIN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -635,6 +847,18 @@ int imin_advanced_greedy(const imin_graph* g, const int32_t* seeds, int32_t n_se
     g_err[0] = '\0';
     return greedy_impl(Driver::kAdvancedGreedy, g, seeds, n_seeds, b, theta, key, out_blockers,
                        out_count, stream);
+}
+
+int imin_batch_advanced_greedy(imin_query* queries, int32_t n_queries, void* stream)
+{
+    g_err[0] = '\0';
+    return batch_impl(Driver::kAdvancedGreedy, queries, n_queries, stream);
+}
+
+int imin_batch_greedy_replace(imin_query* queries, int32_t n_queries, void* stream)
+{
+    g_err[0] = '\0';
+    return batch_impl(Driver::kGreedyReplace, queries, n_queries, stream);
 }
 
 int imin_greedy_replace(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b,

@@ -1,0 +1,282 @@
+// batch.cu -- many independent queries (each with its own graph, seeds, budget, theta and key)
+// advanced together, one greedy round per step: every step is one launch of the block-per-sample
+// kernel over the samples of all queries that are still active, a launch of the whole-graph
+// warp kernel for the rare samples the block tier could not hold, and one selection launch with
+// a block per query. Work items are (query, chunk of samples) pairs handed out by one atomic
+// cursor, so uneven graphs and cascades are load-balanced across the whole GPU. Every query's
+// Philox stream and round numbering are those of the single-query drivers, so each query's
+// result is identical to running it alone.
+#include "internal.h"
+#include "sample_cta.cuh"
+#include "select_dev.cuh"
+
+namespace imin {
+
+namespace {
+
+using namespace cta;
+using namespace sel;
+
+constexpr uint32_t kWholeWarps = 8;  // warps per block of the batched whole-graph kernel
+
+// Largest q with prefix[q] <= item (prefix[0] = 0, item < prefix[nq]).
+__device__ __forceinline__ uint32_t find_query(const unsigned long long* prefix, uint32_t nq,
+                                               unsigned long long item)
+{
+    uint32_t lo = 0, hi = nq;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (prefix[mid] <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Whether query q takes part in step c, and the blocker position that step fills.
+// AdvancedGreedy: steps 0 .. count-1, position c. GreedyReplace: phase 1 at steps 0 .. count-1
+// (position c), phase 2 at steps count .. 2*count-1 (position 2*count-1-c) until its stop flag.
+__device__ __forceinline__ bool step_active(const BatchQuery& Q, const BatchStep& B, int32_t* pos,
+                                            bool* phase2)
+{
+    const int32_t c = static_cast<int32_t>(B.step);
+    *phase2 = false;
+    if (!B.gr) {
+        *pos = c;
+        return c < Q.count;
+    }
+    if (c < Q.count) {
+        *pos = c;
+        return true;
+    }
+    if (c >= 2 * Q.count) return false;
+    if (*reinterpret_cast<const volatile int32_t*>(Q.flags) != 0) return false;
+    *phase2 = true;
+    *pos = 2 * Q.count - 1 - c;
+    return true;
+}
+
+__device__ __forceinline__ SampleParams params_of(const BatchQuery& Q, uint32_t round)
+{
+    SampleParams P{};
+    P.g = Q.g;
+    P.seeds = Q.seeds;
+    P.ns = Q.ns;
+    P.excl = Q.excl;
+    P.key_lo = Q.key_lo;
+    P.key_hi = Q.key_hi;
+    P.round = round;
+    P.theta = Q.theta;
+    P.delta = Q.delta;
+    return P;
+}
+
+__global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCfg C)
+{
+    extern __shared__ __align__(16) uint32_t bm[];
+    __shared__ CtaShared sh;
+    __shared__ unsigned long long s_item;
+    __shared__ uint32_t s_q;
+    __shared__ int s_skip;
+    const uint32_t tid = threadIdx.x;
+    uint8_t* base = C.scratch + static_cast<uint64_t>(blockIdx.x) * C.slot_bytes;
+    Slot S;
+    S.gid = reinterpret_cast<int32_t*>(base + C.off_gid);
+    S.par = reinterpret_cast<uint32_t*>(base + C.off_par);
+    S.idom = reinterpret_cast<uint32_t*>(base + C.off_idom);
+    S.edges = reinterpret_cast<uint2*>(base + C.off_edges);
+    for (uint32_t i = tid; i < C.bm_words; i += kCtaThreads) bm[i] = 0;
+
+    const unsigned long long total = B.prefix[B.nq];
+    SampleCounters sc;
+    unsigned long long examined = 0, live = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned long long item = atomicAdd(&B.ctl->cursor, 1ull);
+            s_item = item;
+            if (item < total) {
+                const uint32_t q = find_query(B.prefix, B.nq, item);
+                int32_t pos;
+                bool ph2;
+                s_q = q;
+                s_skip = !step_active(B.q[q], B, &pos, &ph2);
+            }
+        }
+        __syncthreads();
+        const unsigned long long item = s_item;
+        if (item >= total) break;
+        if (s_skip) continue;
+        const uint32_t q = s_q;
+        const BatchQuery& Q = B.q[q];
+        const SampleParams P = params_of(Q, B.step);
+        const unsigned long long j0 = (item - B.prefix[q]) * B.chunk;
+        const unsigned long long j1 = min(j0 + B.chunk, static_cast<unsigned long long>(Q.theta));
+        for (unsigned long long j = j0; j < j1; ++j) {
+            const int rc = run_sample_cta(P, C, bm, sh, S, static_cast<uint32_t>(j), tid, sc, examined, live);
+            if (tid == 0) {
+                if (rc == kSampleOverflow) {
+                    const uint32_t p = atomicAdd(&B.ctl->over_count, 1u);
+                    if (p < B.over_cap) B.over[p] = make_uint2(q, static_cast<uint32_t>(j));
+                    else atomicOr(&B.ctl->error, kErrCapacity);
+                } else if (rc == kSampleError) {
+                    atomicOr(&B.ctl->error, kErrInternal);
+                }
+            }
+        }
+    }
+    if (B.stats != nullptr) {
+        const uint32_t lane = tid & 31;
+        unsigned long long ex = examined, lv = live;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            ex += __shfl_down_sync(kFull, ex, o);
+            lv += __shfl_down_sync(kFull, lv, o);
+        }
+        unsigned long long* st = B.stats + kTierCta * kStPerTier;
+        if (lane == 0) {
+            if (ex) atomicAdd(st + kStExamined, ex);
+            if (lv) atomicAdd(st + kStLive, lv);
+        }
+        if (tid == 0 && sc.done > 0) {
+            atomicAdd(st + kStSamples, sc.done);
+            atomicAdd(st + kStReached, sc.reached);
+            atomicAdd(st + kStNontree, sc.nontree);
+            atomicAdd(st + kStPasses, sc.passes);
+        }
+    }
+}
+
+// The samples the block tier handed over, one warp each, with whole-graph capacity.
+__global__ void __launch_bounds__(kWholeWarps * 32) k_batch_whole(BatchStep B, TierCfg T)
+{
+    __shared__ __align__(16) uint2 stage[kWholeWarps][kStageCap];
+    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * kWholeWarps + wib;
+    uint8_t* base = T.gscratch + gw * T.warp_bytes;
+    const WarpLayout L = warp_layout(T.rcap, T.hcap, T.ecap, T.dcap, true);
+    WarpSpace<true> w;
+    w.stage = stage[wib];
+    w.lvl = reinterpret_cast<uint32_t*>(base + L.lvl);
+    w.hkey = reinterpret_cast<uint32_t*>(base + L.hkey);
+    w.hval = reinterpret_cast<uint32_t*>(base + L.hval);
+    w.gid = reinterpret_cast<int32_t*>(base + L.gid);
+    w.idom = reinterpret_cast<uint32_t*>(base + L.idom);
+    w.par = reinterpret_cast<uint32_t*>(base + L.par);
+    w.hslot = reinterpret_cast<uint32_t*>(base + L.hslot);
+    w.edges = reinterpret_cast<uint2*>(base + L.edges);
+    w.rcap = T.rcap;
+    w.hcap = T.hcap;
+    w.hbits = T.hbits;
+    w.ecap = T.ecap;
+    w.dcap = T.dcap;
+
+    const uint32_t count = min(*reinterpret_cast<const volatile uint32_t*>(&B.ctl->over_count), B.over_cap);
+    SampleCounters sc;
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(&B.ctl->over_cursor, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= count) break;
+        const uint2 qj = B.over[item];
+        const SampleParams P = params_of(B.q[qj.x], B.step);
+        const int rc = run_sample<true, false>(P, w, qj.y, lane, sc);
+        if (lane == 0 && rc != kSampleDone)
+            atomicOr(&B.ctl->error, rc == kSampleOverflow ? kErrCapacity : kErrInternal);
+    }
+}
+
+// GreedyReplace phase 2, "B <- B \ {u}" for every query in phase 2 at this step.
+__global__ void k_batch_unblock(BatchStep B)
+{
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= B.nq) return;
+    const BatchQuery& Q = B.q[q];
+    int32_t pos;
+    bool ph2;
+    if (!step_active(Q, B, &pos, &ph2) || !ph2) return;
+    const int32_t u = Q.blockers[pos];
+    Q.flags[1] = u;
+    atomicAnd(Q.excl + (u >> 5), ~(1u << (u & 31)));
+}
+
+// One block per query: the strict-max selection of the step (phase-1 candidates are CB).
+__global__ void __launch_bounds__(kSelThreads) k_batch_select(BatchStep B)
+{
+    const BatchQuery& Q = B.q[blockIdx.x];
+    int32_t pos;
+    bool ph2;
+    if (!step_active(Q, B, &pos, &ph2)) return;
+    const bool use_cb = B.gr && !ph2;
+    unsigned long long bd = 0;
+    int32_t bi = kNone;
+    for (int32_t v = threadIdx.x; v < Q.g.n; v += blockDim.x) {
+        const unsigned long long d = Q.delta[v];
+        if (d != 0) Q.delta[v] = 0;
+        const uint32_t bit = 1u << (v & 31);
+        const bool cand = use_cb ? (Q.cb[v >> 5] & bit) != 0 : (Q.excl[v >> 5] & bit) == 0;
+        if (cand && better(d, v, bd, bi)) {
+            bd = d;
+            bi = v;
+        }
+    }
+    block_best<kSelThreads>(bd, bi);
+    if (threadIdx.x == 0 && bi != kNone) {
+        Q.blockers[pos] = bi;
+        Q.excl[bi >> 5] |= 1u << (bi & 31);
+        if (use_cb) Q.cb[bi >> 5] &= ~(1u << (bi & 31));
+        if (ph2 && Q.flags[1] == bi) Q.flags[0] = 1;
+    }
+}
+
+}  // namespace
+
+bool plan_batch_cta(const DeviceInfo& dev, int32_t max_n, int32_t max_m, CtaCfg* c, uint32_t* blocks,
+                    uint64_t* smem, uint64_t* scratch_bytes)
+{
+    uint32_t b0 = 0;
+    uint64_t s0 = 0;
+    if (!plan_cta_tier(dev, max_n, max_m, c, &b0, smem, &s0)) return false;
+    if (cudaFuncSetAttribute(k_batch_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(*smem)) != cudaSuccess)
+        return false;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta, kCtaThreads, *smem);
+    if (occ <= 0) return false;
+    *blocks = static_cast<uint32_t>(occ) * dev.sms;
+    *scratch_bytes = c->slot_bytes * *blocks;
+    return true;
+}
+
+cudaError_t launch_batch_unblock(const BatchStep& B, cudaStream_t s)
+{
+    k_batch_unblock<<<(B.nq + 127) / 128, 128, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_cta(const BatchStep& B, const CtaCfg& c, uint32_t blocks, uint64_t smem,
+                             uint8_t* scratch, cudaStream_t s)
+{
+    CtaCfg cfg = c;
+    cfg.scratch = scratch;
+    k_batch_cta<<<blocks, kCtaThreads, smem, s>>>(B, cfg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_whole(const BatchStep& B, const TierCfg& whole, uint32_t blocks,
+                               uint8_t* scratch, cudaStream_t s)
+{
+    TierCfg t = whole;
+    t.gscratch = scratch;
+    k_batch_whole<<<blocks, kWholeWarps * 32, 0, s>>>(B, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_select(const BatchStep& B, cudaStream_t s)
+{
+    k_batch_select<<<B.nq, kSelThreads, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+uint32_t whole_warps_per_block() { return kWholeWarps; }
+
+}  // namespace imin

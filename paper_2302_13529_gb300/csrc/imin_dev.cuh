@@ -126,6 +126,43 @@ struct CtaCfg {
     uint8_t* scratch;
 };
 
+// One query of a batch (batch.cu): its graph, seed set, masks, counters and results.
+struct BatchQuery {
+    DevGraph g;
+    const int32_t* seeds;
+    uint32_t ns;
+    uint32_t* excl;               // seeds and blocked vertices
+    uint32_t* cb;                 // GreedyReplace phase-1 candidates (N_out(S) \ S)
+    uint32_t key_lo, key_hi;
+    uint32_t theta;
+    unsigned long long* delta;    // [n]
+    int32_t* blockers;            // [b]
+    int32_t count;                // AdvancedGreedy: rounds; GreedyReplace: phase-1 rounds
+    int32_t* flags;               // GreedyReplace: [0] stop flag, [1] vertex unblocked this step
+};
+
+struct BatchCtl {
+    unsigned long long cursor;    // next (query, sample chunk) item
+    uint32_t over_count;          // samples handed to the whole-graph kernel
+    uint32_t over_cursor;
+    uint32_t error;
+    uint32_t pad;
+};
+
+// One greedy step of a batch: round `step` of every query that is still active.
+struct BatchStep {
+    const BatchQuery* q;
+    uint32_t nq;
+    const unsigned long long* prefix;  // [nq+1] first item of each query (inactive: empty)
+    uint32_t chunk;                    // samples per item
+    uint32_t step;
+    int gr;                            // GreedyReplace schedule
+    BatchCtl* ctl;
+    uint2* over;                       // (query, sample) overflow items
+    uint32_t over_cap;
+    unsigned long long* stats;
+};
+
 // Byte layout of one warp's working set (same for shared and global memory).
 struct WarpLayout {
     uint64_t lvl, hkey, hval, gid, idom, par, hslot, edges, total;

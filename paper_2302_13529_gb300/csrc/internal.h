@@ -63,6 +63,17 @@ bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint3
 cudaError_t launch_cta_tier(const SampleParams& P, const CtaCfg& c, uint32_t blocks, uint64_t smem,
                             uint8_t* scratch, cudaStream_t s);
 
+// Batched multi-query steps (batch.cu).
+bool plan_batch_cta(const DeviceInfo& dev, int32_t max_n, int32_t max_m, CtaCfg* c, uint32_t* blocks,
+                    uint64_t* smem, uint64_t* scratch_bytes);
+cudaError_t launch_batch_unblock(const BatchStep& B, cudaStream_t s);
+cudaError_t launch_batch_cta(const BatchStep& B, const CtaCfg& c, uint32_t blocks, uint64_t smem,
+                             uint8_t* scratch, cudaStream_t s);
+cudaError_t launch_batch_whole(const BatchStep& B, const TierCfg& whole, uint32_t blocks,
+                               uint8_t* scratch, cudaStream_t s);
+cudaError_t launch_batch_select(const BatchStep& B, cudaStream_t s);
+uint32_t whole_warps_per_block();
+
 // Selection (Alg. 3/4 argmax) -----------------------------------------------------------------
 struct SelectParams {
     unsigned long long* delta;     // [n]; cleared as it is read

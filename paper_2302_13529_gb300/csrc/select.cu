@@ -6,52 +6,15 @@
 // is the order (larger counter first, then smaller id), which is associative, so the grid can
 // reduce in any order and still return the scan's answer.
 #include "internal.h"
+#include "select_dev.cuh"
 
 namespace imin {
 
 namespace {
 
-constexpr int kSelThreads = 512;
+using namespace sel;
+
 constexpr int kSelBlocksPerSm = 2;
-constexpr int32_t kNone = 0x7FFFFFFF;
-
-__device__ __forceinline__ bool better(unsigned long long d1, int32_t i1, unsigned long long d2,
-                                       int32_t i2)
-{
-    return d1 > d2 || (d1 == d2 && i1 < i2);
-}
-
-__device__ __forceinline__ void warp_best(unsigned long long& d, int32_t& id)
-{
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        const unsigned long long od = __shfl_down_sync(kFull, d, o);
-        const int32_t oi = __shfl_down_sync(kFull, id, o);
-        if (better(od, oi, d, id)) {
-            d = od;
-            id = oi;
-        }
-    }
-}
-
-// Block-wide best of (d, id); result valid in thread 0.
-__device__ __forceinline__ void block_best(unsigned long long& d, int32_t& id)
-{
-    __shared__ unsigned long long sd[kSelThreads / 32];
-    __shared__ int32_t si[kSelThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    warp_best(d, id);
-    if (lane == 0) {
-        sd[wid] = d;
-        si[wid] = id;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        d = lane < kSelThreads / 32 ? sd[lane] : 0ull;
-        id = lane < kSelThreads / 32 ? si[lane] : kNone;
-        warp_best(d, id);
-    }
-}
 
 __global__ void __launch_bounds__(kSelThreads) k_select(SelectParams p)
 {
@@ -69,7 +32,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectParams p)
             bi = v;
         }
     }
-    block_best(bd, bi);
+    block_best<kSelThreads>(bd, bi);
     __shared__ bool last;
     if (threadIdx.x == 0) {
         p.part_d[blockIdx.x] = bd;
@@ -90,7 +53,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectParams p)
             bi = i;
         }
     }
-    block_best(bd, bi);
+    block_best<kSelThreads>(bd, bi);
     if (threadIdx.x == 0) {
         *p.ticket = 0;
         if (bi != kNone) {

@@ -47,6 +47,13 @@ class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64 * 6), ("ms", ctypes.c_double * 6)]
 
 
+class Query(ctypes.Structure):
+    """imin_query of include/imin.h."""
+    _fields_ = [("graph", ctypes.c_void_p), ("seeds", ctypes.c_void_p), ("n_seeds", ctypes.c_int32),
+                ("b", ctypes.c_int32), ("theta", ctypes.c_uint32), ("key", ctypes.c_uint64),
+                ("out_blockers", ctypes.c_void_p), ("out_count", ctypes.c_int32)]
+
+
 KINDS = ("sample_tier0", "sample_tier1", "sample_tier2", "sample_cta", "select", "other")
 
 
@@ -71,6 +78,8 @@ def lib():
         for name in ("imin_advanced_greedy", "imin_greedy_replace"):
             getattr(L, name).argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
                                          ctypes.c_uint64, P, P, P]
+        for name in ("imin_batch_advanced_greedy", "imin_batch_greedy_replace"):
+            getattr(L, name).argtypes = [ctypes.POINTER(Query), ctypes.c_int32, P]
         L.imin_last_stats.argtypes = [ctypes.POINTER(Stats)]
         L.imin_launch_count.restype = ctypes.c_uint64
         L.imin_profile_enable.argtypes = [ctypes.c_int]
@@ -196,6 +205,33 @@ def advanced_greedy(gh: GraphHandle, seeds, b, theta, key, out=None, stream=None
 def greedy_replace(gh: GraphHandle, seeds, b, theta, key, out=None, stream=None):
     """imin_greedy_replace (Alg. 4): blockers in list order."""
     return _greedy(lib().imin_greedy_replace, gh, seeds, b, theta, key, out, stream)
+
+
+def _batch(fn, items, stream):
+    """items: sequence of (GraphHandle, seeds, b, theta, key[, out]) -> list of blocker arrays."""
+    arr = (Query * max(len(items), 1))()
+    keep, outs = [], []
+    for i, it in enumerate(items):
+        gh, seeds, b, theta, key = it[:5]
+        out = it[5] if len(it) > 5 and it[5] is not None else np.zeros(max(int(b), 1), dtype=np.int32)
+        s, ks, ns = _ptr(seeds, np.int32)
+        o, ko, _ = _ptr(out, np.int32)
+        keep += [ks, ko]
+        outs.append(out)
+        arr[i] = Query(gh.handle.value, s.value if s is not None else None, ns, int(b), int(theta),
+                       int(key), o.value, 0)
+    _check(fn(arr, len(items), _stream(stream)))
+    return [outs[i][:arr[i].out_count] for i in range(len(items))]
+
+
+def batch_advanced_greedy(items, stream=None):
+    """imin_batch_advanced_greedy: Alg. 3 for many queries at once (same results as alone)."""
+    return _batch(lib().imin_batch_advanced_greedy, items, stream)
+
+
+def batch_greedy_replace(items, stream=None):
+    """imin_batch_greedy_replace: Alg. 4 for many queries at once (same results as alone)."""
+    return _batch(lib().imin_batch_greedy_replace, items, stream)
 
 
 # ---- measurement hooks ---------------------------------------------------------------------

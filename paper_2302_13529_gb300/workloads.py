@@ -18,8 +18,11 @@ p = 0 are not stored.
 """
 from __future__ import annotations
 
+import ctypes
 import dataclasses
 import math
+import os
+import subprocess
 from fractions import Fraction
 
 import numpy as np
@@ -128,94 +131,65 @@ def _draw_distinct(draw, n: int, m: int, max_batches: int = 64) -> np.ndarray:
     raise RuntimeError("could not draw enough distinct edges; graph too dense for generator")
 
 
-def _chung_lu_offset(n: int, m: int, gamma: float, dmax_frac: float) -> float:
-    """Offset i0 in w_i = (i + i0)^(-1/(gamma-1)) such that the heaviest vertex expects about
-    dmax_frac * n edge endpoints (bisection on i0)."""
-    alpha = 1.0 / (gamma - 1.0)
-    target = max(dmax_frac * n, m / n)
-    idx = np.arange(n, dtype=np.float64)
+_GEN_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "graphgen.c")
+_GEN_LIB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libimin_gen.so")
+_gen = None
 
-    def top(i0):
-        w = (idx + i0) ** (-alpha)
-        return m * w[0] / w.sum()
 
-    lo, hi = 1e-3, float(n)
-    if top(lo) <= target:
-        return lo
-    for _ in range(100):
-        mid = math.sqrt(lo * hi)
-        if top(mid) > target:
-            lo = mid
-        else:
-            hi = mid
-    return hi
+def build_generator(force: bool = False) -> str:
+    """Compile graphgen.c (plain C) into _build/libimin_gen.so."""
+    os.makedirs(os.path.dirname(_GEN_LIB), exist_ok=True)
+    if force or not os.path.exists(_GEN_LIB) or os.path.getmtime(_GEN_LIB) < os.path.getmtime(_GEN_SRC):
+        tmp = _GEN_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _GEN_SRC, "-lm"])
+        os.replace(tmp, _GEN_LIB)
+    return _GEN_LIB
+
+
+def _genlib():
+    global _gen
+    if _gen is None:
+        L = ctypes.CDLL(build_generator())
+        i32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+        L.imin_gen_chung_lu.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_uint64, i32, i32]
+        L.imin_gen_rmat.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_uint64, i32, i32]
+        _gen = L
+    return _gen
 
 
 def chung_lu(n: int, m: int, gamma: float = 2.1, seed: int = 0, dmax_frac: float = 0.1,
              name: str = "") -> tuple[np.ndarray, np.ndarray]:
     """Directed Chung-Lu graph: expected out- and in-weights w_i = (i + i0)^(-1/(gamma-1)),
-    each assigned to vertices by an independent seeded permutation; sources drawn with
-    probability proportional to w_out and targets proportional to w_in; self-loops and
-    duplicates rejected until exactly m distinct edges exist. Returns (row_ptr, col)."""
-    if m > n * (n - 1):
-        raise ValueError("m exceeds n(n-1)")
-    rng = np.random.default_rng(seed)
-    i0 = _chung_lu_offset(n, m, gamma, dmax_frac)
-    base = (np.arange(n, dtype=np.float64) + i0) ** (-1.0 / (gamma - 1.0))
-    w_out = base[rng.permutation(n)]
-    w_in = base[rng.permutation(n)]
-    cdf_out = np.cumsum(w_out)
-    cdf_out /= cdf_out[-1]
-    cdf_in = np.cumsum(w_in)
-    cdf_in /= cdf_in[-1]
-
-    def draw(k):
-        s = np.searchsorted(cdf_out, rng.random(k), side="right")
-        d = np.searchsorted(cdf_in, rng.random(k), side="right")
-        return np.minimum(s, n - 1), np.minimum(d, n - 1)
-
-    keys = _draw_distinct(draw, n, m)
-    return _csr_from_keys(keys, n)
+    each assigned to vertices by an independent seeded permutation, with i0 chosen so that the
+    heaviest vertex expects about dmax_frac * n endpoints; sources drawn with probability
+    proportional to w_out and targets proportional to w_in; self-loops and duplicates rejected
+    until exactly m distinct edges exist (graphgen.c). Returns (row_ptr, col)."""
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    col = np.zeros(max(m, 1), dtype=np.int32)
+    if _genlib().imin_gen_chung_lu(n, m, gamma, dmax_frac, seed & ((1 << 64) - 1), row_ptr, col) != 0:
+        raise ValueError("Chung-Lu generation failed (graph too dense?)")
+    return row_ptr, col[:m]
 
 
 RMAT_ABCD = (0.57, 0.19, 0.19, 0.05)
 
 
-def rmat(scale: int, m: int, abcd=RMAT_ABCD, seed: int = 0, chunk: int = 1 << 22
-         ) -> tuple[np.ndarray, np.ndarray]:
+def rmat(scale: int, m: int, abcd=RMAT_ABCD, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
     """R-MAT graph on n = 2^scale vertices: each edge picks one of four quadrants per level
-    with probabilities (a, b, c, d). Self-loops and duplicates are rejected until exactly m
+    with probabilities (a, b, c, d); self-loops and duplicates are rejected until exactly m
     distinct edges exist, then vertex ids are relabelled by a seeded random permutation (raw
-    R-MAT places the hubs at low ids). Returns (row_ptr, col)."""
-    n = 1 << scale
+    R-MAT places the hubs at low ids) (graphgen.c). Returns (row_ptr, col)."""
     a, b, c, d = abcd
     if abs(a + b + c + d - 1.0) > 1e-9:
         raise ValueError("R-MAT quadrant probabilities must sum to 1")
-    rng = np.random.default_rng(seed)
-    t1, t2, t3 = a, a + b, a + b + c
-
-    def draw(k):
-        out_s = np.empty(k, dtype=np.int64)
-        out_d = np.empty(k, dtype=np.int64)
-        for lo in range(0, k, chunk):
-            kk = min(chunk, k - lo)
-            s = np.zeros(kk, dtype=np.int64)
-            t = np.zeros(kk, dtype=np.int64)
-            for _ in range(scale):
-                r = rng.random(kk)
-                sb = (r >= t2).astype(np.int64)  # quadrants c, d: lower half (source bit 1)
-                db = ((r >= t1) & (r < t2)) | (r >= t3)  # quadrants b, d: right half
-                s = (s << 1) | sb
-                t = (t << 1) | db.astype(np.int64)
-            out_s[lo:lo + kk] = s
-            out_d[lo:lo + kk] = t
-        return out_s, out_d
-
-    keys = _draw_distinct(draw, n, m)
-    perm = rng.permutation(n).astype(np.int64)
-    src = perm[keys // n]
-    dst = perm[keys % n]
-    return _csr_from_keys(src * n + dst, n)
+    n = 1 << scale
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    col = np.zeros(max(m, 1), dtype=np.int32)
+    if _genlib().imin_gen_rmat(scale, m, a, b, c, seed & ((1 << 64) - 1), row_ptr, col) != 0:
+        raise ValueError("R-MAT generation failed")
+    return row_ptr, col[:m]
 
 
 def uniform_seeds(n: int, k: int, seed: int) -> np.ndarray:
