@@ -223,6 +223,7 @@ int setup_query(const imin_graph* g, const std::vector<int32_t>& seeds, uint32_t
     IMIN_CUDA(q.arena.alloc(&q.scratch1, q.plan.scratch_bytes[1]));
     IMIN_CUDA(q.arena.alloc(&q.scratch2, q.plan.scratch_bytes[2]));
     IMIN_CUDA(q.arena.alloc(&q.scratch3, q.plan.scratch_bytes[kTierCta]));
+    if (q.plan.use_cta) IMIN_CUDA(prepare_cta_scratch(q.plan.cta, q.plan.blocks[kTierCta], q.scratch3, s));
     IMIN_CUDA(cudaMemcpyAsync(q.seeds, seeds.data(), sizeof(int32_t) * seeds.size(),
                               cudaMemcpyHostToDevice, s));
     IMIN_CUDA(cudaMemsetAsync(q.excl, 0, sizeof(uint32_t) * q.words, s));
@@ -546,11 +547,25 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         return IMIN_OK;
     }
     const imin_graph* g0 = qs[0].graph;
-    CtaCfg cfg{};
-    uint32_t cta_blocks = 0;
-    uint64_t cta_smem = 0, cta_bytes = 0;
-    if (!plan_batch_cta(g0->dev, max_n, max_m, &cfg, &cta_blocks, &cta_smem, &cta_bytes))
-        return fail(IMIN_ERR_INTERNAL, "the batched block-per-sample kernel cannot be configured");
+    // size classes: the launch of a class reserves the bitmap of its own largest graph
+    std::vector<int> cls(nq);
+    int32_t cls_n[kBatchClasses] = {0, 0, 0}, cls_m[kBatchClasses] = {0, 0, 0};
+    for (int32_t i = 0; i < nq; ++i) {
+        const int32_t n = qs[i].graph->n;
+        cls[i] = n <= (1 << 16) ? 0 : (n <= (1 << 17) ? 1 : 2);
+        cls_n[cls[i]] = std::max(cls_n[cls[i]], n);
+        cls_m[cls[i]] = std::max(cls_m[cls[i]], qs[i].graph->m);
+    }
+    CtaCfg cfg[kBatchClasses] = {};
+    uint32_t cta_blocks[kBatchClasses] = {0, 0, 0};
+    uint64_t cta_smem[kBatchClasses] = {0, 0, 0}, cta_bytes = 0;
+    for (int k = 0; k < kBatchClasses; ++k) {
+        if (cls_n[k] == 0) continue;
+        uint64_t bytes = 0;
+        if (!plan_batch_cta(g0->dev, cls_n[k], cls_m[k], &cfg[k], &cta_blocks[k], &cta_smem[k], &bytes))
+            return fail(IMIN_ERR_INTERNAL, "the batched block-per-sample kernel cannot be configured");
+        cta_bytes = std::max(cta_bytes, bytes);  // the class launches run one after another
+    }
     const TierPlan wp = plan_tiers(g0->dev, max_n, max_m, max_ns);
 
     // per-query device buffers, packed into one allocation
@@ -639,15 +654,22 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
     }
     IMIN_CUDA(cudaMemcpyAsync(dq, hq.data(), sizeof(BatchQuery) * nq, cudaMemcpyHostToDevice, s));
 
-    // per-step item prefixes: an inactive query contributes no items
+    // per-step, per-class item prefixes: queries of other classes and inactive ones contribute
+    // no items
     const uint32_t chunk = static_cast<uint32_t>(std::max<uint64_t>(
-        1, std::min<uint64_t>(64, sum_theta / (static_cast<uint64_t>(cta_blocks) * 16 + 1))));
-    std::vector<unsigned long long> hprefix(static_cast<size_t>(steps) * (nq + 1), 0);
+        1, std::min<uint64_t>(64, sum_theta / (static_cast<uint64_t>(cta_blocks[0] + cta_blocks[1] +
+                                                                     cta_blocks[2]) * 16 + 1))));
+    const size_t stride = static_cast<size_t>(nq) + 1;
+    std::vector<unsigned long long> hprefix(static_cast<size_t>(steps) * kBatchClasses * stride, 0);
+    std::vector<uint8_t> class_busy(static_cast<size_t>(steps) * kBatchClasses, 0);
     for (int32_t c = 0; c < steps; ++c) {
-        unsigned long long* pr = hprefix.data() + static_cast<size_t>(c) * (nq + 1);
-        for (int32_t i = 0; i < nq; ++i) {
-            const bool act = gr ? c < 2 * count[i] : c < count[i];
-            pr[i + 1] = pr[i] + (act ? (qs[i].theta + chunk - 1) / chunk : 0);
+        for (int k = 0; k < kBatchClasses; ++k) {
+            unsigned long long* pr = hprefix.data() + (static_cast<size_t>(c) * kBatchClasses + k) * stride;
+            for (int32_t i = 0; i < nq; ++i) {
+                const bool act = cls[i] == k && (gr ? c < 2 * count[i] : c < count[i]);
+                pr[i + 1] = pr[i] + (act ? (qs[i].theta + chunk - 1) / chunk : 0);
+            }
+            class_busy[static_cast<size_t>(c) * kBatchClasses + k] = pr[nq] > 0;
         }
     }
     unsigned long long* dprefix = nullptr;
@@ -664,7 +686,6 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         BatchStep B{};
         B.q = dq;
         B.nq = static_cast<uint32_t>(nq);
-        B.prefix = dprefix + static_cast<size_t>(c) * (nq + 1);
         B.chunk = chunk;
         B.step = static_cast<uint32_t>(c);
         B.gr = gr ? 1 : 0;
@@ -675,10 +696,18 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         if (gr) {
             IMIN_CUDA(T.run(kKindOther, [&](bool* l) { *l = true; return launch_batch_unblock(B, s); }));
         }
-        IMIN_CUDA(T.run(kKindCta, [&](bool* l) {
-            *l = true;
-            return launch_batch_cta(B, cfg, cta_blocks, cta_smem, cta_scratch, s);
-        }));
+        for (int k = 0; k < kBatchClasses; ++k) {
+            if (!class_busy[static_cast<size_t>(c) * kBatchClasses + k]) continue;
+            BatchStep Bk = B;
+            Bk.cls = static_cast<uint32_t>(k);
+            Bk.prefix = dprefix + (static_cast<size_t>(c) * kBatchClasses + k) * stride;
+            IMIN_CUDA(T.run(kKindCta, [&](bool* l) {
+                *l = true;
+                return launch_batch_cta(Bk, cfg[k], cta_blocks[k], cta_smem[k], cta_scratch, s);
+            }));
+        }
+        // the whole-graph and selection kernels do not read the item prefixes
+        B.prefix = dprefix;
         IMIN_CUDA(T.run(kKindTier2, [&](bool* l) {
             *l = true;
             return launch_batch_whole(B, wp.cfg[kTierWhole], wp.blocks[kTierWhole], whole_scratch, s);

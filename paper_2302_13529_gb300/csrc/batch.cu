@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCf
     for (;;) {
         __syncthreads();
         if (tid == 0) {
-            const unsigned long long item = atomicAdd(&B.ctl->cursor, 1ull);
+            const unsigned long long item = atomicAdd(&B.ctl->cursor[B.cls], 1ull);
             s_item = item;
             if (item < total) {
                 const uint32_t q = find_query(B.prefix, B.nq, item);
@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCf
         const unsigned long long j0 = (item - B.prefix[q]) * B.chunk;
         const unsigned long long j1 = min(j0 + B.chunk, static_cast<unsigned long long>(Q.theta));
         for (unsigned long long j = j0; j < j1; ++j) {
-            const int rc = run_sample_cta(P, C, bm, sh, S, static_cast<uint32_t>(j), tid, sc, examined, live);
+            const int rc = run_sample_cta<true>(P, C, bm, bm, sh, S, static_cast<uint32_t>(j), tid, sc,
+                                                examined, live);
             if (tid == 0) {
                 if (rc == kSampleOverflow) {
                     const uint32_t p = atomicAdd(&B.ctl->over_count, 1u);
@@ -235,7 +236,7 @@ bool plan_batch_cta(const DeviceInfo& dev, int32_t max_n, int32_t max_m, CtaCfg*
 {
     uint32_t b0 = 0;
     uint64_t s0 = 0;
-    if (!plan_cta_tier(dev, max_n, max_m, c, &b0, smem, &s0)) return false;
+    if (max_n > kCtaMaxVertices || !plan_cta_tier(dev, max_n, max_m, c, &b0, smem, &s0)) return false;
     if (cudaFuncSetAttribute(k_batch_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(*smem)) != cudaSuccess)
         return false;

@@ -117,12 +117,14 @@ struct TierCfg {
 
 // Block-per-sample tier (sample_cta.cu): per-block slot layout and shared-memory sizes.
 struct CtaCfg {
-    uint32_t bm_words;    // visited bitmap words (>= n/32), also the resolution hash space
-    uint32_t res_slots;   // resolution hash slots (power of two; keys + values fit in bm_words)
+    uint32_t bm_words;    // visited bitmap words (>= n/32)
+    uint32_t res_slots;   // resolution hash slots (power of two)
     uint32_t res_shift;   // 32 - log2(res_slots)
-    uint32_t rcap;        // local ids per slot (n + 1: never exceeded)
+    uint32_t rcap;        // local ids per slot
     uint32_t ecap;        // non-tree edges per slot
-    uint64_t off_gid, off_par, off_idom, off_edges, slot_bytes;
+    uint32_t global_bitmap;  // 1: the bitmap is in the slot (large n); 0: in shared memory,
+                             // where it also holds the resolution hash
+    uint64_t off_bm, off_gid, off_par, off_idom, off_edges, slot_bytes;
     uint8_t* scratch;
 };
 
@@ -141,8 +143,12 @@ struct BatchQuery {
     int32_t* flags;               // GreedyReplace: [0] stop flag, [1] vertex unblocked this step
 };
 
+// Queries of a batch are grouped by visited-bitmap size (n <= 2^16, 2^17, 2^18) so that each
+// group's launch reserves only the shared memory its largest graph needs.
+constexpr int kBatchClasses = 3;
+
 struct BatchCtl {
-    unsigned long long cursor;    // next (query, sample chunk) item
+    unsigned long long cursor[kBatchClasses];  // next (query, sample chunk) item of each class
     uint32_t over_count;          // samples handed to the whole-graph kernel
     uint32_t over_cursor;
     uint32_t error;
@@ -153,8 +159,10 @@ struct BatchCtl {
 struct BatchStep {
     const BatchQuery* q;
     uint32_t nq;
-    const unsigned long long* prefix;  // [nq+1] first item of each query (inactive: empty)
+    const unsigned long long* prefix;  // [nq+1] first item of each query in this launch's class
+                                       // (queries of other classes and inactive ones: empty)
     uint32_t chunk;                    // samples per item
+    uint32_t cls;                      // size class of this launch
     uint32_t step;
     int gr;                            // GreedyReplace schedule
     BatchCtl* ctl;

@@ -57,11 +57,14 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns);
 cudaError_t launch_sample_tier(int tier, const SampleParams& P, const TierPlan& plan,
                                uint8_t* scratch, cudaStream_t s, bool* launched);
 
-// Block-per-sample tier (graphs with n <= kCtaMaxVertices): layout, grid and shared memory.
+// Block-per-sample tier: layout, grid and shared memory. Graphs with n <= kCtaMaxVertices keep
+// the visited bitmap in shared memory; larger ones keep it in each block's global slot.
 bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint32_t* blocks, uint64_t* smem,
                    uint64_t* scratch_bytes);
 cudaError_t launch_cta_tier(const SampleParams& P, const CtaCfg& c, uint32_t blocks, uint64_t smem,
                             uint8_t* scratch, cudaStream_t s);
+// Zero the per-slot visited bitmaps of a large-graph block tier (no-op for the shared variant).
+cudaError_t prepare_cta_scratch(const CtaCfg& c, uint32_t blocks, uint8_t* scratch, cudaStream_t s);
 
 // Batched multi-query steps (batch.cu).
 bool plan_batch_cta(const DeviceInfo& dev, int32_t max_n, int32_t max_m, CtaCfg* c, uint32_t* blocks,

@@ -14,9 +14,13 @@ namespace {
 
 using namespace cta;
 
+// kSmemBitmap: the visited bitmap lives in shared memory (n <= 2^18) and doubles as the
+// resolution hash; otherwise it lives in the block's global slot and the dynamic shared memory
+// holds only the resolution hash.
+template <bool kSmemBitmap>
 __global__ void __launch_bounds__(kCtaThreads, 8) k_sample_cta(SampleParams P, CtaCfg C)
 {
-    extern __shared__ __align__(16) uint32_t bm[];
+    extern __shared__ __align__(16) uint32_t dsm[];
     __shared__ CtaShared sh;
     const uint32_t tid = threadIdx.x;
     if (P.done != nullptr && *reinterpret_cast<const volatile int32_t*>(P.done) != 0) return;
@@ -27,8 +31,12 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_sample_cta(SampleParams P, C
     S.par = reinterpret_cast<uint32_t*>(base + C.off_par);
     S.idom = reinterpret_cast<uint32_t*>(base + C.off_idom);
     S.edges = reinterpret_cast<uint2*>(base + C.off_edges);
+    uint32_t* bm = kSmemBitmap ? dsm : reinterpret_cast<uint32_t*>(base + C.off_bm);
 
-    for (uint32_t i = tid; i < C.bm_words; i += kCtaThreads) bm[i] = 0;
+    // a shared bitmap starts dirty; a global one is zeroed by the host and kept clean
+    if constexpr (kSmemBitmap) {
+        for (uint32_t i = tid; i < C.bm_words; i += kCtaThreads) bm[i] = 0;
+    }
     SampleCounters sc;
     unsigned long long examined = 0, live = 0;
     for (;;) {
@@ -37,7 +45,7 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_sample_cta(SampleParams P, C
         __syncthreads();
         const uint32_t j = sh.item;
         if (j >= P.theta) break;
-        const int rc = run_sample_cta(P, C, bm, sh, S, j, tid, sc, examined, live);
+        const int rc = run_sample_cta<kSmemBitmap>(P, C, bm, dsm, sh, S, j, tid, sc, examined, live);
         if (tid == 0) {
             if (rc == kSampleOverflow) {
                 const uint32_t pos = atomicAdd(&P.ctl->count[kTierWhole], 1u);
@@ -76,37 +84,60 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_sample_cta(SampleParams P, C
 bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint32_t* blocks, uint64_t* smem,
                    uint64_t* scratch_bytes)
 {
-    if (n > kCtaMaxVertices) return false;
-    const uint32_t words = std::max<uint32_t>((static_cast<uint32_t>(n) + 31) / 32, 2048);
+    const bool smem_bitmap = n <= kCtaMaxVertices;
+    const uint32_t nwords = (static_cast<uint32_t>(n) + 31) / 32;
     uint32_t slots = 1;
-    while (2 * slots * 2 <= words) slots <<= 1;  // keys + values fit in the bitmap space
-    c->bm_words = words;
+    if (smem_bitmap) {
+        c->bm_words = std::max<uint32_t>(nwords, 2048);
+        while (2 * slots * 2 <= c->bm_words) slots <<= 1;  // keys + values fit in the bitmap space
+    } else {
+        c->bm_words = nwords;
+        slots = 4096;  // 32 KB of shared memory for the resolution hash
+    }
+    c->global_bitmap = smem_bitmap ? 0u : 1u;
     c->res_slots = slots;
     uint32_t bits = 0;
     while ((1u << bits) < slots) ++bits;
     c->res_shift = 32 - bits;
-    c->rcap = static_cast<uint32_t>(n) + 1;
+    // every reached vertex fits when the bitmap is shared; large graphs cap the slot arrays and
+    // hand bigger cascades to the whole-graph tier
+    c->rcap = smem_bitmap ? static_cast<uint32_t>(n) + 1
+                          : static_cast<uint32_t>(std::min<int64_t>(static_cast<int64_t>(n) + 1, 1 << 18));
     c->ecap = static_cast<uint32_t>(std::min<int64_t>(16384, std::max<int64_t>(m, 1)));
     if (const char* cap = std::getenv("IMIN_CTA_EDGE_CAP")) {  // test hook: force overflows
         const uint32_t v = static_cast<uint32_t>(std::strtoul(cap, nullptr, 10));
         if (v > 0) c->ecap = std::min(c->ecap, v);
     }
     uint64_t o = 0;
+    c->off_bm = o;    o = align16(o + (smem_bitmap ? 0ull : 4ull * c->bm_words));
     c->off_gid = o;   o = align16(o + 4ull * c->rcap);
     c->off_par = o;   o = align16(o + 4ull * c->rcap);
     c->off_idom = o;  o = align16(o + 4ull * c->rcap);
     c->off_edges = o; o = align16(o + 8ull * c->ecap);
     c->slot_bytes = (o + 255) & ~255ull;
-    *smem = 4ull * words;
+    *smem = smem_bitmap ? 4ull * c->bm_words : 8ull * slots;
     if (*smem > dev.smem_optin) return false;
-    cudaFuncSetAttribute(k_sample_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(*smem));
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta, kCtaThreads, *smem);
+    if (smem_bitmap) {
+        cudaFuncSetAttribute(k_sample_cta<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(*smem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta<true>, kCtaThreads, *smem);
+    } else {
+        cudaFuncSetAttribute(k_sample_cta<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(*smem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta<false>, kCtaThreads, *smem);
+    }
     if (occ <= 0) return false;
     *blocks = static_cast<uint32_t>(occ) * dev.sms;
     *scratch_bytes = c->slot_bytes * *blocks;
     return true;
+}
+
+cudaError_t prepare_cta_scratch(const CtaCfg& c, uint32_t blocks, uint8_t* scratch, cudaStream_t s)
+{
+    if (!c.global_bitmap) return cudaSuccess;
+    // zero every slot's bitmap (the kernel keeps them zero afterwards)
+    return cudaMemset2DAsync(scratch + c.off_bm, c.slot_bytes, 0, 4ull * c.bm_words, blocks, s);
 }
 
 cudaError_t launch_cta_tier(const SampleParams& P, const CtaCfg& c, uint32_t blocks, uint64_t smem,
@@ -114,7 +145,8 @@ cudaError_t launch_cta_tier(const SampleParams& P, const CtaCfg& c, uint32_t blo
 {
     CtaCfg cfg = c;
     cfg.scratch = scratch;
-    k_sample_cta<<<blocks, kCtaThreads, smem, s>>>(P, cfg);
+    if (c.global_bitmap) k_sample_cta<false><<<blocks, kCtaThreads, smem, s>>>(P, cfg);
+    else k_sample_cta<true><<<blocks, kCtaThreads, smem, s>>>(P, cfg);
     return cudaGetLastError();
 }
 

@@ -146,8 +146,11 @@ __device__ __forceinline__ void visit_staged(const SampleParams& P, const CtaCfg
     }
 }
 
+// bm: visited bitmap (shared or global memory); res: 2 * C.res_slots words of shared memory for
+// the non-tree target resolution -- the bitmap itself when kResInBitmap (it is cleared first).
+template <bool kResInBitmap>
 __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCfg& C, uint32_t* bm,
-                                              CtaShared& sh, const Slot& S, uint32_t j,
+                                              uint32_t* res, CtaShared& sh, const Slot& S, uint32_t j,
                                               uint32_t tid, SampleCounters& sc,
                                               unsigned long long& examined, unsigned long long& live)
 {
@@ -291,8 +294,8 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
     // non-tree edge targets: global id -> local id through a hash in the bitmap space, in
     // chunks of at most half the hash's slots
     if (nE > 0) {
-        uint32_t* keys = bm;
-        uint32_t* vals = bm + C.res_slots;
+        uint32_t* keys = res;
+        uint32_t* vals = res + C.res_slots;
         const uint32_t hmask = C.res_slots - 1;
         for (uint32_t c0 = 0; c0 < nE; c0 += C.res_slots / 2) {
             const uint32_t c1 = min(nE, c0 + C.res_slots / 2);
@@ -313,7 +316,9 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
             }
             __syncthreads();
         }
-        for (uint32_t i = tid; i < 2 * C.res_slots; i += kCtaThreads) bm[i] = 0;
+        if constexpr (kResInBitmap) {
+            for (uint32_t i = tid; i < 2 * C.res_slots; i += kCtaThreads) bm[i] = 0;
+        }
         broken = __syncthreads_or(broken);
         if (broken) return kSampleError;
     }

@@ -226,3 +226,15 @@ def test_many_seeds(cuda_lib, monkeypatch, disable_block_tier):
     gh = cuda_lib.load_graph(g)
     got = cuda_lib.estimate_decrease(gh, seeds, [], 500, 4242, 1)
     assert np.array_equal(got, O.decrease(g, seeds, [], 500, 4242, 1))
+
+
+def test_large_graph_global_bitmap_tier(cuda_lib):
+    """n = 2^19 > 2^18: the block tier keeps its visited bitmap in global memory."""
+    g = W.graph_rmat_wc(19, 1 << 20, seed=91)
+    seeds = W.uniform_seeds(g.n, 30, 92)
+    gh = cuda_lib.load_graph(g)
+    got, st = cuda_lib.estimate_decrease(gh, seeds, [], 3000, 93, 1, stats=True)
+    assert np.array_equal(got, O.decrease(g, seeds, [], 3000, 93, 1))
+    assert st["tier_samples"][3] > 0
+    B = cuda_lib.advanced_greedy(gh, seeds, 3, 1000, 94)
+    assert np.array_equal(B, O.advanced_greedy(g, seeds, 3, 1000, 94))
