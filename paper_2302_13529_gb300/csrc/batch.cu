@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCf
     S.gid = reinterpret_cast<int32_t*>(base + C.off_gid);
     S.par = reinterpret_cast<uint32_t*>(base + C.off_par);
     S.idom = reinterpret_cast<uint32_t*>(base + C.off_idom);
+    S.rows = reinterpret_cast<int2*>(base + C.off_rows);
     S.edges = reinterpret_cast<uint2*>(base + C.off_edges);
     for (uint32_t i = tid; i < C.bm_words; i += kCtaThreads) bm[i] = 0;
 

@@ -124,7 +124,8 @@ struct CtaCfg {
     uint32_t ecap;        // non-tree edges per slot
     uint32_t global_bitmap;  // 1: the bitmap is in the slot (large n); 0: in shared memory,
                              // where it also holds the resolution hash
-    uint64_t off_bm, off_gid, off_par, off_idom, off_edges, slot_bytes;
+    uint32_t tree_words;     // shared words free after the BFS for a copy of idom and c
+    uint64_t off_bm, off_gid, off_par, off_idom, off_rows, off_edges, slot_bytes;
     uint8_t* scratch;
 };
 

@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_sample_cta(SampleParams P, C
     S.gid = reinterpret_cast<int32_t*>(base + C.off_gid);
     S.par = reinterpret_cast<uint32_t*>(base + C.off_par);
     S.idom = reinterpret_cast<uint32_t*>(base + C.off_idom);
+    S.rows = reinterpret_cast<int2*>(base + C.off_rows);
     S.edges = reinterpret_cast<uint2*>(base + C.off_edges);
     uint32_t* bm = kSmemBitmap ? dsm : reinterpret_cast<uint32_t*>(base + C.off_bm);
 
@@ -95,6 +96,7 @@ bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint3
         slots = 4096;  // 32 KB of shared memory for the resolution hash
     }
     c->global_bitmap = smem_bitmap ? 0u : 1u;
+    c->tree_words = smem_bitmap ? c->bm_words : 2 * slots;
     c->res_slots = slots;
     uint32_t bits = 0;
     while ((1u << bits) < slots) ++bits;
@@ -113,6 +115,7 @@ bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint3
     c->off_gid = o;   o = align16(o + 4ull * c->rcap);
     c->off_par = o;   o = align16(o + 4ull * c->rcap);
     c->off_idom = o;  o = align16(o + 4ull * c->rcap);
+    c->off_rows = o;  o = align16(o + 8ull * c->rcap);
     c->off_edges = o; o = align16(o + 8ull * c->ecap);
     c->slot_bytes = (o + 255) & ~255ull;
     *smem = smem_bitmap ? 4ull * c->bm_words : 8ull * slots;

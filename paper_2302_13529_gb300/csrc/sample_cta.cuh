@@ -7,12 +7,14 @@
 //   * visited set: an n-bit bitmap in shared memory; discovering a vertex is one shared-memory
 //     atomicOr, so no cascade size ever overflows the visited structure;
 //   * BFS level by level, 256 frontier vertices per block-wide scan: their out-edges are
-//     flattened into 4-edge groups; each thread takes 2 consecutive groups (one binary search
-//     for the owner row, two independent Philox4x32-10 chains), loads each group's 4 thresholds
-//     with one 16-byte load and decides them with one Philox call;
-//   * live edges (a few percent of the examined ones) are staged per warp and then visited by
-//     the whole warp: target load, visited test-and-set, and one shared atomic per warp to
-//     hand out local ids (ballot + popcount), so the rare live edges do not serialise the warp;
+//     flattened into 4-edge groups; each thread takes one group per iteration (binary search
+//     for the owner row), loads its 4 thresholds with one 16-byte load and decides them with
+//     one Philox4x32-10 call;
+//   * live edges (a few percent of the examined ones) accumulate in a per-warp stage across
+//     iterations and are visited by the whole warp once the stage is half full (and at the end
+//     of each chunk): target load, visited test-and-set, and one shared atomic per warp to hand
+//     out local ids (ballot + popcount). Batching the visits keeps the dependent target loads
+//     and ballots off the per-iteration path and all 32 lanes busy when they run;
 //   * per-vertex arrays indexed by local id (BFS discovery order) -- global id, BFS parent,
 //     immediate dominator -- live in a per-block slot of global memory that is written once
 //     per discovery and read back densely, so it streams through L2;
@@ -35,8 +37,8 @@ constexpr uint32_t kCtaThreads = 128;
 constexpr uint32_t kCtaWarps = kCtaThreads / 32;
 constexpr uint32_t kVpt = 2;                        // frontier vertices per thread per chunk
 constexpr uint32_t kChunk = kCtaThreads * kVpt;     // frontier vertices per chunk
-constexpr uint32_t kGpt = 2;                        // consecutive 4-edge groups per thread
-constexpr uint32_t kStage = 32 * 4;                 // live edges staged per warp and group slot
+constexpr uint32_t kStage = 192;                    // live edges staged per warp (visited once
+                                                    // another full iteration might not fit)
 constexpr uint32_t kCtaLevels = 512;
 
 struct CtaShared {
@@ -89,6 +91,7 @@ struct Slot {
     int32_t* gid;
     uint32_t* par;   // BFS parent; reused for subtree sizes after the dominator passes
     uint32_t* idom;
+    int2* rows;      // [row_ptr[v], row_ptr[v+1]) of every reached vertex, read at its level
     uint2* edges;
 };
 
@@ -103,10 +106,12 @@ __device__ __forceinline__ void visit_staged(const SampleParams& P, const CtaCfg
         const bool act = s0 + lane < count;
         bool disc = false, nt = false;
         uint32_t ul = 0, v = 0;
+        int2 row = make_int2(0, 0);
         if (act) {
             const uint2 c = stage[s0 + lane];
             ul = c.x;
             v = static_cast<uint32_t>(__ldg(P.g.col + c.y));
+            row = make_int2(__ldg(P.g.row_ptr + v), __ldg(P.g.row_ptr + v + 1));
             if (!excluded(P.excl, v)) {
                 ++lv;
                 const uint32_t bit = 1u << (v & 31);
@@ -126,6 +131,7 @@ __device__ __forceinline__ void visit_staged(const SampleParams& P, const CtaCfg
                     S.gid[lid] = static_cast<int32_t>(v);
                     S.par[lid] = ul;
                     S.idom[lid] = ul;
+                    S.rows[lid] = row;
                 } else {
                     sh.flag = 1;
                 }
@@ -146,6 +152,69 @@ __device__ __forceinline__ void visit_staged(const SampleParams& P, const CtaCfg
     }
 }
 
+// Loads of words that other threads update with atomics (idom, c): L2 for global memory,
+// volatile for shared memory.
+template <bool G>
+__device__ __forceinline__ uint32_t ld_tree(const uint32_t* p)
+{
+    if constexpr (G) return __ldcg(p);
+    else return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+// Immediate dominators by folding NCA(idom(v), p, parent(v)) over the non-tree edges until a pass
+// changes nothing, then subtree sizes (deepest level first) and Delta += c for reached
+// non-seeds. idom and c are either shared-memory copies (G = false) or the slot arrays (G = true;
+// c then reuses the parent array, which is dead once the passes end). Returns true when the
+// iteration failed its bounds (cannot happen for a well-formed sample).
+template <bool G>
+__device__ __forceinline__ bool finish_tree(const SampleParams& P, CtaShared& sh, const Slot& S,
+                                            uint32_t* idom, uint32_t* c, uint32_t nR, uint32_t nE,
+                                            uint32_t nlev, uint32_t ns, uint32_t tid, uint32_t* passes_out)
+{
+    bool broken = false;
+    uint32_t passes = 0;
+    if (nE > 0) {
+        for (;;) {
+            int changed = 0;
+            for (uint32_t k = tid; k < nE; k += kCtaThreads) {
+                const uint2 e = S.edges[k];
+                uint32_t a = ld_tree<G>(idom + e.y), b = e.x;
+                for (uint32_t g = 0; a != b; ++g) {
+                    if (g > 2 * nR) { broken = true; a = 0; break; }
+                    if (a > b) a = ld_tree<G>(idom + a);
+                    else b = ld_tree<G>(idom + b);
+                }
+                b = S.par[e.y];
+                for (uint32_t g = 0; a != b; ++g) {
+                    if (g > 2 * nR) { broken = true; a = 0; break; }
+                    if (a > b) a = ld_tree<G>(idom + a);
+                    else b = ld_tree<G>(idom + b);
+                }
+                if (!broken && a < ld_tree<G>(idom + e.y)) {
+                    const uint32_t old = atomicMin(idom + e.y, a);
+                    changed |= a < old;
+                }
+            }
+            ++passes;
+            broken = __syncthreads_or(broken);
+            if (broken || !__syncthreads_or(changed)) break;
+            if (passes > nR + 1) { broken = true; break; }
+        }
+    }
+    *passes_out = passes;
+    for (uint32_t i = tid; i < nR; i += kCtaThreads) c[i] = 1;
+    __syncthreads();
+    for (uint32_t d = nlev - 1; d >= 1; --d) {
+        const uint32_t b0 = sh.lvl[d], b1 = sh.lvl[d + 1];
+        for (uint32_t i = b0 + tid; i < b1; i += kCtaThreads) atomicAdd(c + ld_tree<G>(idom + i), ld_tree<G>(c + i));
+        __syncthreads();
+    }
+    for (uint32_t i = 1 + ns + tid; i < nR; i += kCtaThreads)
+        atomicAdd(P.delta + S.gid[i], static_cast<unsigned long long>(ld_tree<G>(c + i)));
+    __syncthreads();
+    return broken;
+}
+
 // bm: visited bitmap (shared or global memory); res: 2 * C.res_slots words of shared memory for
 // the non-tree target resolution -- the bitmap itself when kResInBitmap (it is cleared first).
 template <bool kResInBitmap>
@@ -157,9 +226,11 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
     const uint32_t ns = P.ns;
     const uint32_t lane = tid & 31, wid = tid >> 5;
     for (uint32_t i = tid; i < ns; i += kCtaThreads) {
-        S.gid[1 + i] = P.seeds[i];
+        const int32_t u = P.seeds[i];
+        S.gid[1 + i] = u;
         S.idom[1 + i] = 0;
         S.par[1 + i] = 0;
+        S.rows[1 + i] = make_int2(__ldg(P.g.row_ptr + u), __ldg(P.g.row_ptr + u + 1));
     }
     if (tid == 0) {
         S.idom[0] = 0;
@@ -186,9 +257,9 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
                 beg[k] = 0;
                 end[k] = 0;
                 if (idx < le) {
-                    const int32_t u = S.gid[idx];
-                    beg[k] = __ldg(P.g.row_ptr + u);
-                    end[k] = __ldg(P.g.row_ptr + u + 1);
+                    const int2 row = S.rows[idx];
+                    beg[k] = row.x;
+                    end[k] = row.y;
                 }
                 ex += static_cast<uint32_t>(end[k] - beg[k]);
                 ng[k] = end[k] > beg[k]
@@ -207,61 +278,66 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
             }
             __syncthreads();
 
-            // ---- groups: kGpt consecutive per thread, one owner search per thread
-            for (uint32_t t0 = 0; t0 < total; t0 += kCtaThreads * kGpt) {
-                const uint32_t tb = t0 + tid * kGpt;
-                uint32_t p = 0;
-                if (tb < total) {
+            // ---- groups: one per thread per iteration; live edges accumulate in the warp's
+            // stage, which is visited by the full warp whenever it is at least half full and
+            // once more at the end of the chunk
+            uint32_t staged = 0;  // warp-uniform
+            // the owner row and thresholds of the thread's next group are fetched while the
+            // current group's Philox runs
+            uint32_t nq = 0, nul = 0;
+            int32_t nob = 0, noe = 0;
+            uint4 nth = make_uint4(0, 0, 0, 0);
+            auto fetch = [&](uint32_t t) {
+                nob = 0;
+                noe = 0;
+                if (t < total) {
+                    uint32_t p = 0;
 #pragma unroll
                     for (uint32_t step = kChunk / 2; step >= 1; step >>= 1)
-                        if (sh.incl[p + step - 1] <= tb) p += step;
+                        if (sh.incl[p + step - 1] <= t) p += step;
+                    nob = sh.beg[p];
+                    noe = sh.end[p];
+                    const uint32_t first = p ? sh.incl[p - 1] : 0u;
+                    nq = (static_cast<uint32_t>(nob) >> 2) + (t - first);
+                    nul = base + p;
+                    nth = __ldg(P.g.thr4 + nq);
                 }
-                uint32_t q[kGpt], ul[kGpt];
-                int32_t ob[kGpt], oe[kGpt];
-                uint4 th[kGpt];
-#pragma unroll
-                for (uint32_t k = 0; k < kGpt; ++k) {
-                    const uint32_t t = tb + k;
-                    ob[k] = 0;
-                    oe[k] = 0;
-                    q[k] = 0;
-                    ul[k] = 0;
-                    if (t < total) {
-                        while (sh.incl[p] <= t) ++p;  // next non-empty row (t < total keeps p in range)
-                        ob[k] = sh.beg[p];
-                        oe[k] = sh.end[p];
-                        const uint32_t first = p ? sh.incl[p - 1] : 0u;
-                        q[k] = (static_cast<uint32_t>(ob[k]) >> 2) + (t - first);
-                        ul[k] = base + p;
-                        th[k] = __ldg(P.g.thr4 + q[k]);
-                    }
+            };
+            fetch(tid);
+            for (uint32_t t0 = 0; t0 < total; t0 += kCtaThreads) {
+                const uint32_t q = nq, ul = nul;
+                const int32_t ob = nob, oe = noe;
+                const uint4 th = nth;
+                fetch(t0 + kCtaThreads + tid);
+                uint32_t m = 0;
+                if (oe > ob) {
+                    const uint4 r = philox4x32_10(make_uint4(q, j, P.round, 0u), P.key_lo, P.key_hi);
+                    const int32_t e0 = static_cast<int32_t>(q << 2);
+                    m |= (e0 + 0 >= ob && e0 + 0 < oe && r.x <= th.x) ? 1u : 0u;
+                    m |= (e0 + 1 >= ob && e0 + 1 < oe && r.y <= th.y) ? 2u : 0u;
+                    m |= (e0 + 2 >= ob && e0 + 2 < oe && r.z <= th.z) ? 4u : 0u;
+                    m |= (e0 + 3 >= ob && e0 + 3 < oe && r.w <= th.w) ? 8u : 0u;
                 }
-#pragma unroll
-                for (uint32_t k = 0; k < kGpt; ++k) {
-                    uint32_t m = 0;
-                    if (oe[k] > ob[k]) {
-                        const uint4 r = philox4x32_10(make_uint4(q[k], j, P.round, 0u), P.key_lo, P.key_hi);
-                        const int32_t e0 = static_cast<int32_t>(q[k] << 2);
-                        m |= (e0 + 0 >= ob[k] && e0 + 0 < oe[k] && r.x <= th[k].x) ? 1u : 0u;
-                        m |= (e0 + 1 >= ob[k] && e0 + 1 < oe[k] && r.y <= th[k].y) ? 2u : 0u;
-                        m |= (e0 + 2 >= ob[k] && e0 + 2 < oe[k] && r.z <= th[k].z) ? 4u : 0u;
-                        m |= (e0 + 3 >= ob[k] && e0 + 3 < oe[k] && r.w <= th[k].w) ? 8u : 0u;
-                    }
-                    // stage this lane's live edges of group slot k, then visit them as a warp
-                    const uint32_t nc = __popc(m);
-                    const uint32_t cincl = warp_incl_scan(nc, lane);
-                    const uint32_t ctot = __shfl_sync(kFull, cincl, 31);
-                    if (ctot == 0) continue;
-                    uint32_t w = cincl - nc;
-                    while (m) {
-                        const uint32_t i = __ffs(m) - 1;
-                        m &= m - 1;
-                        sh.stage[wid][w++] = make_uint2(ul[k], (q[k] << 2) + i);
-                    }
+                const uint32_t nc = __popc(m);
+                const uint32_t cincl = warp_incl_scan(nc, lane);
+                uint32_t w = staged + cincl - nc;
+                while (m) {
+                    const uint32_t i = __ffs(m) - 1;
+                    m &= m - 1;
+                    sh.stage[wid][w++] = make_uint2(ul, (q << 2) + i);
+                }
+                staged += __shfl_sync(kFull, cincl, 31);
+                if (staged > kStage - 32 * 4) {  // the next iteration could overflow the stage
                     __syncwarp();
-                    visit_staged(P, C, bm, sh, S, sh.stage[wid], ctot, lane, lv);
+                    visit_staged(P, C, bm, sh, S, sh.stage[wid], staged, lane, lv);
                     __syncwarp();
+                    staged = 0;
                 }
+            }
+            if (staged > 0) {
+                __syncwarp();
+                visit_staged(P, C, bm, sh, S, sh.stage[wid], staged, lane, lv);
+                __syncwarp();
             }
             __syncthreads();
         }
@@ -323,50 +399,22 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
         if (broken) return kSampleError;
     }
 
-    // immediate dominators: fold NCA(idom(v), p, parent(v)) over the non-tree edges
+    // dominators, subtree sizes and counter update: on a shared-memory copy of the tree when it
+    // fits the (now free) resolution space, else on the slot arrays
     uint32_t passes = 0;
-    if (nE > 0) {
-        for (;;) {
-            int changed = 0;
-            for (uint32_t k = tid; k < nE; k += kCtaThreads) {
-                const uint2 e = S.edges[k];
-                uint32_t a = __ldcg(S.idom + e.y), b = e.x;
-                for (uint32_t g = 0; a != b; ++g) {
-                    if (g > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = __ldcg(S.idom + a);
-                    else b = __ldcg(S.idom + b);
-                }
-                b = S.par[e.y];
-                for (uint32_t g = 0; a != b; ++g) {
-                    if (g > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = __ldcg(S.idom + a);
-                    else b = __ldcg(S.idom + b);
-                }
-                if (!broken && a < __ldcg(S.idom + e.y)) {
-                    const uint32_t old = atomicMin(S.idom + e.y, a);
-                    changed |= a < old;
-                }
-            }
-            ++passes;
-            broken = __syncthreads_or(broken);
-            if (broken || !__syncthreads_or(changed)) break;
-            if (passes > nR + 1) { broken = true; break; }
-        }
-    }
-
-    // subtree sizes, deepest level first (c reuses the parent array)
-    uint32_t* c = S.par;
-    for (uint32_t i = tid; i < nR; i += kCtaThreads) c[i] = 1;
-    __syncthreads();
-    for (uint32_t d = nlev - 1; d >= 1; --d) {
-        const uint32_t b0 = sh.lvl[d], b1 = sh.lvl[d + 1];
-        for (uint32_t i = b0 + tid; i < b1; i += kCtaThreads)
-            atomicAdd(c + __ldcg(S.idom + i), __ldcg(c + i));
+    if (2 * nR <= C.tree_words) {
+        uint32_t* sidom = res;
+        uint32_t* sc_ = res + nR;
+        for (uint32_t i = tid; i < nR; i += kCtaThreads) sidom[i] = S.idom[i];
         __syncthreads();
+        broken = finish_tree<false>(P, sh, S, sidom, sc_, nR, nE, nlev, ns, tid, &passes);
+        if constexpr (kResInBitmap) {
+            for (uint32_t i = tid; i < 2 * nR; i += kCtaThreads) res[i] = 0;  // it is the bitmap
+            __syncthreads();
+        }
+    } else {
+        broken = finish_tree<true>(P, sh, S, S.idom, S.par, nR, nE, nlev, ns, tid, &passes);
     }
-    for (uint32_t i = 1 + ns + tid; i < nR; i += kCtaThreads)
-        atomicAdd(P.delta + S.gid[i], static_cast<unsigned long long>(__ldcg(c + i)));
-    __syncthreads();
 
     if (tid == 0) {
         sc.reached += nR - 1;

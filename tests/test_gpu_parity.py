@@ -238,3 +238,27 @@ def test_large_graph_global_bitmap_tier(cuda_lib):
     assert st["tier_samples"][3] > 0
     B = cuda_lib.advanced_greedy(gh, seeds, 3, 1000, 94)
     assert np.array_equal(B, O.advanced_greedy(g, seeds, 3, 1000, 94))
+
+
+# --------------------------------------------------------------------------------------------
+# large workload: R-MAT 2^22 / 2^26, WC, |S| = 200 (block tier with the bitmap in global memory)
+# --------------------------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def rmat22():
+    return W.rmat22_query()
+
+
+def test_rmat22_counters(cuda_lib, rmat22, monkeypatch):
+    """At full graph size: the first 2,000 sampled graphs of a call against the oracle, and a
+    20,000-sample call of the block tier against the warp-tier pipeline (an independent GPU
+    implementation of the same sample routine)."""
+    q = rmat22
+    gh = cuda_lib.load_graph(q.graph)
+    got = cuda_lib.estimate_decrease(gh, q.seeds, [], 2000, q.key, 0)
+    want = oracle_pool.decrease(q.graph, q.seeds, [], 2000, q.key, 0)
+    assert np.array_equal(got, want)
+    a = cuda_lib.estimate_decrease(gh, q.seeds, [], 20_000, q.key, 5)
+    monkeypatch.setenv("IMIN_DISABLE_CTA_TIER", "1")
+    b = cuda_lib.estimate_decrease(gh, q.seeds, [], 20_000, q.key, 5)
+    assert np.array_equal(a, b)
