@@ -7,6 +7,7 @@
 // stream-ordered allocator and are released on the same stream.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -107,6 +108,62 @@ struct CallTimer {
                 g_prof_launches[kind] += 1;
             }
         }
+    }
+};
+
+// Captures the launches of a driver's rounds into one CUDA graph and launches it. Capture runs on
+// a private stream that first waits for the caller's stream (the legacy default stream cannot be
+// captured); the caller's stream then waits for the graph. Disabled while per-kernel profiling
+// is on (events between launches) and by IMIN_NO_GRAPHS=1.
+struct GraphScope {
+    cudaStream_t user = nullptr, cap = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool on = false, capturing = false;
+
+    static bool enabled()
+    {
+        const char* v = std::getenv("IMIN_NO_GRAPHS");
+        return !(v && *v && *v != '0') && g_profile_on.load() == 0;
+    }
+    cudaError_t begin(cudaStream_t s)
+    {
+        user = s;
+        on = enabled();
+        if (!on) return cudaSuccess;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, user);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, ev, 0);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        capturing = e == cudaSuccess;
+        return e;
+    }
+    cudaStream_t stream() const { return on ? cap : user; }
+    cudaError_t end()
+    {
+        if (!on) return cudaSuccess;
+        capturing = false;
+        cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, cap);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, cap);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(user, ev, 0);
+        return e;
+    }
+    ~GraphScope()
+    {
+        if (capturing) {  // an error left the capture open: close and drop it
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(cap, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (ev) cudaEventDestroy(ev);
+        if (cap) cudaStreamDestroy(cap);
     }
 };
 
@@ -424,12 +481,16 @@ int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t
     std::vector<RoundCtl> hctl;
     RoundCtl* ctl = nullptr;
     CallTimer T(s);
+    GraphScope G;
     if (which == Driver::kAdvancedGreedy) {
         count = std::min<int32_t>(b, g->n - n_seeds);
         if (count > 0) {
             IMIN_CUDA(q.arena.alloc(&ctl, count));
             IMIN_CUDA(cudaMemsetAsync(ctl, 0, sizeof(RoundCtl) * count, s));
         }
+        IMIN_CUDA(G.begin(s));
+        T.s = G.stream();
+        T.on = T.on && !G.on;
         for (int32_t i = 0; i < count; ++i) {
             const SampleParams P = sample_params(g, q, n_seeds, theta, key, static_cast<uint32_t>(i),
                                                  ctl + i, nullptr);
@@ -437,6 +498,7 @@ int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t
             sp.pos = i;
             IMIN_CUDA(enqueue_select(sp, T));
         }
+        IMIN_CUDA(G.end());
         hctl.resize(count);
     } else {
         uint32_t* cb = nullptr;
@@ -456,6 +518,10 @@ int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t
             IMIN_CUDA(q.arena.alloc(&ctl, calls));
             IMIN_CUDA(cudaMemsetAsync(ctl, 0, sizeof(RoundCtl) * calls, s));
         }
+        IMIN_CUDA(G.begin(s));
+        T.s = G.stream();
+        T.on = T.on && !G.on;
+        const cudaStream_t rs = G.stream();
         uint32_t round = 0;
         // phase 1: greedy over the seeds' out-neighbours
         for (int32_t i = 0; i < count; ++i, ++round) {
@@ -470,7 +536,7 @@ int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t
         for (int32_t i = count - 1; i >= 0; --i, ++round) {
             IMIN_CUDA(T.run(kKindOther, [&](bool* launched) {
                 *launched = true;
-                return launch_unblock(q.excl, dB, i, flags, flags + 1, s);
+                return launch_unblock(q.excl, dB, i, flags, flags + 1, rs);
             }));
             const SampleParams P = sample_params(g, q, n_seeds, theta, key, round, ctl + round, flags);
             IMIN_CUDA(enqueue_call(P, q, T));
@@ -480,6 +546,7 @@ int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t
             p2.cur = flags + 1;
             IMIN_CUDA(enqueue_select(p2, T));
         }
+        IMIN_CUDA(G.end());
         hctl.resize(calls);
     }
 
@@ -682,6 +749,11 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
     IMIN_CUDA(cudaMemsetAsync(ctl, 0, sizeof(BatchCtl) * std::max(steps, 1), s));
 
     CallTimer T(s);
+    GraphScope G;
+    IMIN_CUDA(G.begin(s));
+    T.s = G.stream();
+    T.on = T.on && !G.on;
+    const cudaStream_t rs = G.stream();
     for (int32_t c = 0; c < steps; ++c) {
         BatchStep B{};
         B.q = dq;
@@ -694,7 +766,7 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         B.over_cap = static_cast<uint32_t>(std::min<uint64_t>(sum_theta, 0xFFFFFFFFull));
         B.stats = stats;
         if (gr) {
-            IMIN_CUDA(T.run(kKindOther, [&](bool* l) { *l = true; return launch_batch_unblock(B, s); }));
+            IMIN_CUDA(T.run(kKindOther, [&](bool* l) { *l = true; return launch_batch_unblock(B, rs); }));
         }
         for (int k = 0; k < kBatchClasses; ++k) {
             if (!class_busy[static_cast<size_t>(c) * kBatchClasses + k]) continue;
@@ -703,17 +775,18 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
             Bk.prefix = dprefix + (static_cast<size_t>(c) * kBatchClasses + k) * stride;
             IMIN_CUDA(T.run(kKindCta, [&](bool* l) {
                 *l = true;
-                return launch_batch_cta(Bk, cfg[k], cta_blocks[k], cta_smem[k], cta_scratch, s);
+                return launch_batch_cta(Bk, cfg[k], cta_blocks[k], cta_smem[k], cta_scratch, rs);
             }));
         }
         // the whole-graph and selection kernels do not read the item prefixes
         B.prefix = dprefix;
         IMIN_CUDA(T.run(kKindTier2, [&](bool* l) {
             *l = true;
-            return launch_batch_whole(B, wp.cfg[kTierWhole], wp.blocks[kTierWhole], whole_scratch, s);
+            return launch_batch_whole(B, wp.cfg[kTierWhole], wp.blocks[kTierWhole], whole_scratch, rs);
         }));
-        IMIN_CUDA(T.run(kKindSelect, [&](bool* l) { *l = true; return launch_batch_select(B, s); }));
+        IMIN_CUDA(T.run(kKindSelect, [&](bool* l) { *l = true; return launch_batch_select(B, rs); }));
     }
+    IMIN_CUDA(G.end());
 
     std::vector<BatchCtl> hctl(std::max(steps, 1));
     std::vector<int32_t> hblk(std::max<uint64_t>(blk_off[nq], 1));

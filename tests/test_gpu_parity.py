@@ -262,3 +262,25 @@ def test_rmat22_counters(cuda_lib, rmat22, monkeypatch):
     monkeypatch.setenv("IMIN_DISABLE_CTA_TIER", "1")
     b = cuda_lib.estimate_decrease(gh, q.seeds, [], 20_000, q.key, 5)
     assert np.array_equal(a, b)
+
+
+def test_cuda_graph_capture_matches_plain_launches(cuda_lib, tiny, monkeypatch):
+    """The greedy rounds run as one captured CUDA graph by default; IMIN_NO_GRAPHS=1 launches them
+    one by one. Both must give the same blockers (and the oracle's)."""
+    q = tiny
+    gh = cuda_lib.load_graph(q.graph)
+    g_ag = cuda_lib.advanced_greedy(gh, q.seeds, q.b, 3000, q.key)
+    g_gr = cuda_lib.greedy_replace(gh, q.seeds, q.b, 3000, q.key)
+    g_bt = cuda_lib.batch_greedy_replace([(gh, q.seeds, q.b, 3000, q.key), (gh, q.seeds[:3], 4, 500, 7)])
+    monkeypatch.setenv("IMIN_NO_GRAPHS", "1")
+    assert np.array_equal(g_ag, cuda_lib.advanced_greedy(gh, q.seeds, q.b, 3000, q.key))
+    assert np.array_equal(g_gr, cuda_lib.greedy_replace(gh, q.seeds, q.b, 3000, q.key))
+    p_bt = cuda_lib.batch_greedy_replace([(gh, q.seeds, q.b, 3000, q.key), (gh, q.seeds[:3], 4, 500, 7)])
+    assert all(np.array_equal(a, b) for a, b in zip(g_bt, p_bt))
+    assert np.array_equal(g_ag, O.advanced_greedy(q.graph, q.seeds, q.b, 3000, q.key))
+    # a non-default caller stream
+    import torch
+    monkeypatch.delenv("IMIN_NO_GRAPHS")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        assert np.array_equal(g_ag, cuda_lib.advanced_greedy(gh, q.seeds, q.b, 3000, q.key))
