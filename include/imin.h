@@ -46,6 +46,7 @@ extern "C" {
 #define IMIN_ERR_NOMEM (-3)     /* device memory could not be allocated */
 #define IMIN_ERR_CAPACITY (-4)  /* a sampled cascade exceeded the largest kernel tier */
 #define IMIN_ERR_INTERNAL (-5)  /* a kernel reported an internal consistency failure */
+#define IMIN_ERR_TIMEOUT (-6)   /* imin_server_wait: the request is not finished yet */
 
 /* Opaque handle: a directed graph resident in device memory. */
 typedef struct imin_graph imin_graph;
@@ -140,8 +141,9 @@ int imin_estimate_decrease_noalloc(const imin_graph* g, const int32_t* seeds, in
  * still active, load-balanced over the whole GPU, followed by one selection launch with a block
  * per query. Each query's result (blockers and count) is identical to what
  * imin_advanced_greedy / imin_greedy_replace return for it alone (same random streams, same
- * round numbering, same tie rule). Graphs must all live on the current device. When a graph has
- * more than 2^18 vertices the batch runs its queries one at a time. */
+ * round numbering, same tie rule). Graphs must all live on the current device. Queries are
+ * grouped by graph size so that each group's launch reserves only the memory its largest graph
+ * needs. */
 typedef struct imin_query {
     const imin_graph* graph;  /* in: loaded graph */
     const int32_t* seeds;     /* in: n_seeds distinct vertex ids (host or device) */
@@ -159,6 +161,52 @@ int imin_batch_advanced_greedy(imin_query* queries, int32_t n_queries, void* str
 
 /* Alg. 4 for every query of `queries`; GreedyReplace's phase-2 early stop is per query. */
 int imin_batch_greedy_replace(imin_query* queries, int32_t n_queries, void* stream);
+
+/* ---- serving: continuous batching of queries --------------------------------------------
+ * A server owns a worker thread and a CUDA stream on the current device. Requests (an
+ * AdvancedGreedy or GreedyReplace query on a loaded graph) are admitted in arrival order
+ * whenever a batch slot is free and their device state (about 8n + n/4 bytes plus seeds and
+ * blockers) fits the memory budget. Every step advances all admitted requests by one greedy
+ * round in shared launches (one Alg. 2 launch per graph-size class over the sampled graphs of
+ * every admitted request, then one selection launch); a request admitted at step t runs its own
+ * rounds 0, 1, ... at steps t, t+1, ..., so its random stream and result are exactly those of
+ * imin_advanced_greedy / imin_greedy_replace called alone. Finished requests leave between
+ * steps and free their slot and memory. Graphs must stay loaded until their requests finish. */
+typedef struct imin_server imin_server;
+
+typedef struct imin_server_config {
+    uint64_t memory_budget;  /* bytes of request state the server may hold (0: 1/4 of free memory) */
+    int32_t max_active;      /* batch slots (0: 256) */
+    int32_t reserved;
+} imin_server_config;
+
+typedef struct imin_server_stats {
+    uint64_t submitted, admitted, completed;
+    uint64_t steps;          /* batched steps run */
+    uint64_t samples;        /* sampled graphs processed */
+    uint64_t memory_in_use;  /* bytes of admitted request state */
+    uint64_t pending;        /* requests waiting for admission */
+} imin_server_stats;
+
+int imin_server_create(const imin_server_config* cfg, imin_server** out);
+
+/* Queue a request. driver: 0 = AdvancedGreedy (Alg. 3), 1 = GreedyReplace (Alg. 4). seeds (host or
+ * device) are copied. Never waits for the GPU. *ticket identifies the request for
+ * imin_server_wait. Errors: IMIN_ERR_INVALID, IMIN_ERR_NOMEM (state larger than the whole
+ * budget), or the server's fatal error after a failed step. Thread-safe. */
+int imin_server_submit(imin_server* srv, int32_t driver, const imin_graph* g, const int32_t* seeds,
+                       int32_t n_seeds, int32_t b, uint32_t theta, uint64_t key, uint64_t* ticket);
+
+/* Wait up to timeout_ms (negative: forever) for a request; on success copies its blockers
+ * (host int32[capacity]) and count, reports the latency from submission to completion in
+ * milliseconds, and releases the ticket. IMIN_ERR_TIMEOUT leaves the ticket valid. */
+int imin_server_wait(imin_server* srv, uint64_t ticket, int64_t timeout_ms, int32_t* out_blockers,
+                     int32_t capacity, int32_t* out_count, double* latency_ms);
+
+int imin_server_get_stats(imin_server* srv, imin_server_stats* out);
+
+/* Finish all submitted requests, stop the worker and release the server. */
+int imin_server_destroy(imin_server* srv);
 
 /* Work counters of one Alg. 2 call, for throughput accounting (not part of the method). */
 typedef struct imin_stats {

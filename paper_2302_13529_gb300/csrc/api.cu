@@ -587,7 +587,6 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
     std::vector<std::vector<int32_t>> hseeds(nq);
     int32_t max_n = 0, max_m = 0;
     uint32_t max_ns = 0;
-    bool fits = true;
     for (int32_t i = 0; i < nq; ++i) {
         imin_query& Q = qs[i];
         Q.out_count = 0;
@@ -601,37 +600,28 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         max_n = std::max(max_n, Q.graph->n);
         max_m = std::max(max_m, Q.graph->m);
         max_ns = std::max<uint32_t>(max_ns, static_cast<uint32_t>(Q.n_seeds));
-        fits = fits && Q.graph->n <= kCtaMaxVertices;
-    }
-    if (!fits) {
-        // graphs above the block tier's size run one query at a time
-        for (int32_t i = 0; i < nq; ++i) {
-            imin_query& Q = qs[i];
-            int rc = greedy_impl(which, Q.graph, Q.seeds, Q.n_seeds, Q.b, Q.theta, Q.key,
-                                 Q.out_blockers, &Q.out_count, stream);
-            if (rc) return rc;
-        }
-        return IMIN_OK;
     }
     const imin_graph* g0 = qs[0].graph;
     // size classes: the launch of a class reserves the bitmap of its own largest graph
     std::vector<int> cls(nq);
-    int32_t cls_n[kBatchClasses] = {0, 0, 0}, cls_m[kBatchClasses] = {0, 0, 0};
+    int32_t cls_n[kBatchClasses] = {}, cls_m[kBatchClasses] = {};
     for (int32_t i = 0; i < nq; ++i) {
-        const int32_t n = qs[i].graph->n;
-        cls[i] = n <= (1 << 16) ? 0 : (n <= (1 << 17) ? 1 : 2);
-        cls_n[cls[i]] = std::max(cls_n[cls[i]], n);
+        cls[i] = batch_class(qs[i].graph->n);
+        cls_n[cls[i]] = std::max(cls_n[cls[i]], qs[i].graph->n);
         cls_m[cls[i]] = std::max(cls_m[cls[i]], qs[i].graph->m);
     }
     CtaCfg cfg[kBatchClasses] = {};
-    uint32_t cta_blocks[kBatchClasses] = {0, 0, 0};
-    uint64_t cta_smem[kBatchClasses] = {0, 0, 0}, cta_bytes = 0;
+    uint32_t cta_blocks[kBatchClasses] = {};
+    uint64_t cta_smem[kBatchClasses] = {}, cta_bytes = 0, global_bytes = 0;
     for (int k = 0; k < kBatchClasses; ++k) {
         if (cls_n[k] == 0) continue;
         uint64_t bytes = 0;
         if (!plan_batch_cta(g0->dev, cls_n[k], cls_m[k], &cfg[k], &cta_blocks[k], &cta_smem[k], &bytes))
             return fail(IMIN_ERR_INTERNAL, "the batched block-per-sample kernel cannot be configured");
-        cta_bytes = std::max(cta_bytes, bytes);  // the class launches run one after another
+        // the shared-bitmap classes run one after another on one buffer; the global-bitmap
+        // class keeps its own, whose bitmaps must stay zero between samples
+        if (k == kBatchGlobalClass) global_bytes = bytes;
+        else cta_bytes = std::max(cta_bytes, bytes);
     }
     const TierPlan wp = plan_tiers(g0->dev, max_n, max_m, max_ns);
 
@@ -667,7 +657,11 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
     IMIN_CUDA(arena.alloc(&dseeds, seed_off[nq]));
     IMIN_CUDA(arena.alloc(&dblk, std::max<uint64_t>(blk_off[nq], 1)));
     IMIN_CUDA(arena.alloc(&dq, nq));
+    uint8_t* global_scratch = nullptr;
     IMIN_CUDA(arena.alloc(&cta_scratch, cta_bytes));
+    IMIN_CUDA(arena.alloc(&global_scratch, global_bytes));
+    if (global_bytes > 0)
+        IMIN_CUDA(prepare_cta_scratch(cfg[kBatchGlobalClass], cta_blocks[kBatchGlobalClass], global_scratch, s));
     IMIN_CUDA(arena.alloc(&whole_scratch, wp.scratch_bytes[kTierWhole]));
     IMIN_CUDA(arena.alloc(&stats, kStCount));
     IMIN_CUDA(arena.alloc(&over, sum_theta));
@@ -717,6 +711,8 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         d.blockers = dblk + blk_off[i];
         d.count = count[i];
         d.flags = reinterpret_cast<int32_t*>(buf + off[i].flags);
+        d.start = 0;
+        d.gr = gr ? 1 : 0;
         steps = std::max(steps, gr ? 2 * count[i] : count[i]);
     }
     IMIN_CUDA(cudaMemcpyAsync(dq, hq.data(), sizeof(BatchQuery) * nq, cudaMemcpyHostToDevice, s));
@@ -725,7 +721,7 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
     // no items
     const uint32_t chunk = static_cast<uint32_t>(std::max<uint64_t>(
         1, std::min<uint64_t>(64, sum_theta / (static_cast<uint64_t>(cta_blocks[0] + cta_blocks[1] +
-                                                                     cta_blocks[2]) * 16 + 1))));
+                                                                     cta_blocks[2] + cta_blocks[3]) * 16 + 1))));
     const size_t stride = static_cast<size_t>(nq) + 1;
     std::vector<unsigned long long> hprefix(static_cast<size_t>(steps) * kBatchClasses * stride, 0);
     std::vector<uint8_t> class_busy(static_cast<size_t>(steps) * kBatchClasses, 0);
@@ -760,12 +756,11 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         B.nq = static_cast<uint32_t>(nq);
         B.chunk = chunk;
         B.step = static_cast<uint32_t>(c);
-        B.gr = gr ? 1 : 0;
         B.ctl = ctl + c;
         B.over = over;
         B.over_cap = static_cast<uint32_t>(std::min<uint64_t>(sum_theta, 0xFFFFFFFFull));
         B.stats = stats;
-        if (gr) {
+        if (gr) {  // phase-2 unblocking of every GreedyReplace query at this step
             IMIN_CUDA(T.run(kKindOther, [&](bool* l) { *l = true; return launch_batch_unblock(B, rs); }));
         }
         for (int k = 0; k < kBatchClasses; ++k) {
@@ -775,7 +770,8 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
             Bk.prefix = dprefix + (static_cast<size_t>(c) * kBatchClasses + k) * stride;
             IMIN_CUDA(T.run(kKindCta, [&](bool* l) {
                 *l = true;
-                return launch_batch_cta(Bk, cfg[k], cta_blocks[k], cta_smem[k], cta_scratch, rs);
+                return launch_batch_cta(Bk, cfg[k], cta_blocks[k], cta_smem[k],
+                                        k == kBatchGlobalClass ? global_scratch : cta_scratch, rs);
             }));
         }
         // the whole-graph and selection kernels do not read the item prefixes

@@ -32,15 +32,19 @@ __device__ __forceinline__ uint32_t find_query(const unsigned long long* prefix,
     return lo;
 }
 
-// Whether query q takes part in step c, and the blocker position that step fills.
-// AdvancedGreedy: steps 0 .. count-1, position c. GreedyReplace: phase 1 at steps 0 .. count-1
-// (position c), phase 2 at steps count .. 2*count-1 (position 2*count-1-c) until its stop flag.
+// Whether query q takes part in this step, and the blocker position the step fills. With
+// c = step - start (the query's own round): AdvancedGreedy rounds 0 .. count-1 fill position c;
+// GreedyReplace phase 1 (rounds 0 .. count-1) fills position c, phase 2 (rounds count ..
+// 2*count-1) refills position 2*count-1-c until its stop flag is set.
 __device__ __forceinline__ bool step_active(const BatchQuery& Q, const BatchStep& B, int32_t* pos,
                                             bool* phase2)
 {
-    const int32_t c = static_cast<int32_t>(B.step);
+    if (B.step < Q.start) return false;
+    const uint32_t cu = B.step - Q.start;
+    if (cu > 0x7FFFFFFFu) return false;
+    const int32_t c = static_cast<int32_t>(cu);
     *phase2 = false;
-    if (!B.gr) {
+    if (!Q.gr) {
         *pos = c;
         return c < Q.count;
     }
@@ -70,9 +74,10 @@ __device__ __forceinline__ SampleParams params_of(const BatchQuery& Q, uint32_t 
     return P;
 }
 
+template <bool kSmemBitmap>
 __global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCfg C)
 {
-    extern __shared__ __align__(16) uint32_t bm[];
+    extern __shared__ __align__(16) uint32_t dsm[];
     __shared__ CtaShared sh;
     __shared__ unsigned long long s_item;
     __shared__ uint32_t s_q;
@@ -85,7 +90,10 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCf
     S.idom = reinterpret_cast<uint32_t*>(base + C.off_idom);
     S.rows = reinterpret_cast<int2*>(base + C.off_rows);
     S.edges = reinterpret_cast<uint2*>(base + C.off_edges);
-    for (uint32_t i = tid; i < C.bm_words; i += kCtaThreads) bm[i] = 0;
+    uint32_t* bm = kSmemBitmap ? dsm : reinterpret_cast<uint32_t*>(base + C.off_bm);
+    if constexpr (kSmemBitmap) {
+        for (uint32_t i = tid; i < C.bm_words; i += kCtaThreads) bm[i] = 0;
+    }
 
     const unsigned long long total = B.prefix[B.nq];
     SampleCounters sc;
@@ -109,12 +117,12 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCf
         if (s_skip) continue;
         const uint32_t q = s_q;
         const BatchQuery& Q = B.q[q];
-        const SampleParams P = params_of(Q, B.step);
+        const SampleParams P = params_of(Q, B.step - Q.start);
         const unsigned long long j0 = (item - B.prefix[q]) * B.chunk;
         const unsigned long long j1 = min(j0 + B.chunk, static_cast<unsigned long long>(Q.theta));
         for (unsigned long long j = j0; j < j1; ++j) {
-            const int rc = run_sample_cta<true>(P, C, bm, bm, sh, S, static_cast<uint32_t>(j), tid, sc,
-                                                examined, live);
+            const int rc = run_sample_cta<kSmemBitmap>(P, C, bm, dsm, sh, S, static_cast<uint32_t>(j), tid,
+                                                       sc, examined, live);
             if (tid == 0) {
                 if (rc == kSampleOverflow) {
                     const uint32_t p = atomicAdd(&B.ctl->over_count, 1u);
@@ -180,7 +188,7 @@ __global__ void __launch_bounds__(kWholeWarps * 32) k_batch_whole(BatchStep B, T
         item = __shfl_sync(kFull, item, 0);
         if (item >= count) break;
         const uint2 qj = B.over[item];
-        const SampleParams P = params_of(B.q[qj.x], B.step);
+        const SampleParams P = params_of(B.q[qj.x], B.step - B.q[qj.x].start);
         const int rc = run_sample<true, false>(P, w, qj.y, lane, sc);
         if (lane == 0 && rc != kSampleDone)
             atomicOr(&B.ctl->error, rc == kSampleOverflow ? kErrCapacity : kErrInternal);
@@ -208,7 +216,7 @@ __global__ void __launch_bounds__(kSelThreads) k_batch_select(BatchStep B)
     int32_t pos;
     bool ph2;
     if (!step_active(Q, B, &pos, &ph2)) return;
-    const bool use_cb = B.gr && !ph2;
+    const bool use_cb = Q.gr && !ph2;
     unsigned long long bd = 0;
     int32_t bi = kNone;
     for (int32_t v = threadIdx.x; v < Q.g.n; v += blockDim.x) {
@@ -237,12 +245,15 @@ bool plan_batch_cta(const DeviceInfo& dev, int32_t max_n, int32_t max_m, CtaCfg*
 {
     uint32_t b0 = 0;
     uint64_t s0 = 0;
-    if (max_n > kCtaMaxVertices || !plan_cta_tier(dev, max_n, max_m, c, &b0, smem, &s0)) return false;
-    if (cudaFuncSetAttribute(k_batch_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(*smem)) != cudaSuccess)
-        return false;
+    if (!plan_cta_tier(dev, max_n, max_m, c, &b0, smem, &s0)) return false;
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta, kCtaThreads, *smem);
+    if (c->global_bitmap) {
+        if (allow_max_dynamic_smem(k_batch_cta<false>, dev) != cudaSuccess) return false;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta<false>, kCtaThreads, *smem);
+    } else {
+        if (allow_max_dynamic_smem(k_batch_cta<true>, dev) != cudaSuccess) return false;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta<true>, kCtaThreads, *smem);
+    }
     if (occ <= 0) return false;
     *blocks = static_cast<uint32_t>(occ) * dev.sms;
     *scratch_bytes = c->slot_bytes * *blocks;
@@ -260,7 +271,8 @@ cudaError_t launch_batch_cta(const BatchStep& B, const CtaCfg& c, uint32_t block
 {
     CtaCfg cfg = c;
     cfg.scratch = scratch;
-    k_batch_cta<<<blocks, kCtaThreads, smem, s>>>(B, cfg);
+    if (c.global_bitmap) k_batch_cta<false><<<blocks, kCtaThreads, smem, s>>>(B, cfg);
+    else k_batch_cta<true><<<blocks, kCtaThreads, smem, s>>>(B, cfg);
     return cudaGetLastError();
 }
 

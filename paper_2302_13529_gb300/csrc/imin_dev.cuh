@@ -142,11 +142,20 @@ struct BatchQuery {
     int32_t* blockers;            // [b]
     int32_t count;                // AdvancedGreedy: rounds; GreedyReplace: phase-1 rounds
     int32_t* flags;               // GreedyReplace: [0] stop flag, [1] vertex unblocked this step
+    uint32_t start;               // step at which the query joined: its round is step - start
+    int32_t gr;                   // 1: GreedyReplace schedule, 0: AdvancedGreedy
 };
 
-// Queries of a batch are grouped by visited-bitmap size (n <= 2^16, 2^17, 2^18) so that each
+// Queries of a batch are grouped by visited-bitmap size (n <= 2^16, 2^17, 2^18 with the bitmap
+// in shared memory; larger graphs with the bitmap in each block's global slot) so that each
 // group's launch reserves only the shared memory its largest graph needs.
-constexpr int kBatchClasses = 3;
+constexpr int kBatchClasses = 4;
+constexpr int kBatchGlobalClass = 3;
+
+__host__ __device__ inline int batch_class(int32_t n)
+{
+    return n <= (1 << 16) ? 0 : (n <= (1 << 17) ? 1 : (n <= kCtaMaxVertices ? 2 : kBatchGlobalClass));
+}
 
 struct BatchCtl {
     unsigned long long cursor[kBatchClasses];  // next (query, sample chunk) item of each class
@@ -165,7 +174,6 @@ struct BatchStep {
     uint32_t chunk;                    // samples per item
     uint32_t cls;                      // size class of this launch
     uint32_t step;
-    int gr;                            // GreedyReplace schedule
     BatchCtl* ctl;
     uint2* over;                       // (query, sample) overflow items
     uint32_t over_cap;

@@ -17,6 +17,19 @@ struct DeviceInfo {
 
 DeviceInfo device_info();
 
+// Let `func` launch with up to the device's opt-in shared memory (minus its static shared
+// memory). Raising the limit once means that plans made for different graph sizes never lower
+// it under a launch that needs more; occupancy still follows each launch's actual size.
+template <typename F>
+cudaError_t allow_max_dynamic_smem(F func, const DeviceInfo& dev)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, func);
+    if (e != cudaSuccess) return e;
+    const int avail = static_cast<int>(dev.smem_optin) - static_cast<int>(a.sharedSizeBytes);
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, avail > 0 ? avail : 0);
+}
+
 // Record `msg` as the calling thread's last error (fixed buffer, no allocation); returns code.
 int fail_msg(int code, const char* msg);
 

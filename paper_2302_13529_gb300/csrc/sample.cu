@@ -167,8 +167,7 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns)
         p.scratch_bytes[0] = 0;
         int occ = 0;
         if (p.smem_bytes[0] <= dev.smem_optin) {
-            cudaFuncSetAttribute(k_sample_tier<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(p.smem_bytes[0]));
+            allow_max_dynamic_smem(k_sample_tier<0>, dev);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_tier<0>,
                                                           kWarpsPerBlock * 32, p.smem_bytes[0]);
         }

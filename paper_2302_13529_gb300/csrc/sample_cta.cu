@@ -122,12 +122,10 @@ bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint3
     if (*smem > dev.smem_optin) return false;
     int occ = 0;
     if (smem_bitmap) {
-        cudaFuncSetAttribute(k_sample_cta<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(*smem));
+        allow_max_dynamic_smem(k_sample_cta<true>, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta<true>, kCtaThreads, *smem);
     } else {
-        cudaFuncSetAttribute(k_sample_cta<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(*smem));
+        allow_max_dynamic_smem(k_sample_cta<false>, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta<false>, kCtaThreads, *smem);
     }
     if (occ <= 0) return false;

@@ -15,8 +15,9 @@ import numpy as np
 from .build import LIB
 
 IMIN_OK = 0
+IMIN_ERR_TIMEOUT = -6
 ERRORS = {-1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
-          -4: "capacity exceeded", -5: "internal error"}
+          -4: "capacity exceeded", -5: "internal error", -6: "not finished yet"}
 
 _lib = None
 
@@ -54,6 +55,16 @@ class Query(ctypes.Structure):
                 ("out_blockers", ctypes.c_void_p), ("out_count", ctypes.c_int32)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_uint64), ("max_active", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "admitted", "completed", "steps",
+                                                "samples", "memory_in_use", "pending")]
+
+
 KINDS = ("sample_tier0", "sample_tier1", "sample_tier2", "sample_cta", "select", "other")
 
 
@@ -80,6 +91,14 @@ def lib():
                                          ctypes.c_uint64, P, P, P]
         for name in ("imin_batch_advanced_greedy", "imin_batch_greedy_replace"):
             getattr(L, name).argtypes = [ctypes.POINTER(Query), ctypes.c_int32, P]
+        L.imin_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
+        L.imin_server_submit.argtypes = [P, ctypes.c_int32, P, P, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_uint32, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_uint64)]
+        L.imin_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_int64, P, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+        L.imin_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+        L.imin_server_destroy.argtypes = [P]
         L.imin_last_stats.argtypes = [ctypes.POINTER(Stats)]
         L.imin_launch_count.restype = ctypes.c_uint64
         L.imin_profile_enable.argtypes = [ctypes.c_int]
@@ -232,6 +251,54 @@ def batch_advanced_greedy(items, stream=None):
 def batch_greedy_replace(items, stream=None):
     """imin_batch_greedy_replace: Alg. 4 for many queries at once (same results as alone)."""
     return _batch(lib().imin_batch_greedy_replace, items, stream)
+
+
+class Server:
+    """Continuous-batching request server (imin_server_*): submit queries at any time; each is
+    admitted when a batch slot and its device memory are available, advanced one greedy round per
+    shared step with all other admitted requests, and returns exactly the result of running it
+    alone."""
+
+    AG, GR = 0, 1
+
+    def __init__(self, memory_budget: int = 0, max_active: int = 0):
+        cfg = ServerConfig(int(memory_budget), int(max_active), 0)
+        h = ctypes.c_void_p()
+        _check(lib().imin_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, driver, gh: GraphHandle, seeds, b, theta, key) -> int:
+        s, ks, ns = _ptr(seeds, np.int32)
+        t = ctypes.c_uint64()
+        _check(lib().imin_server_submit(self._h, int(driver), gh.handle, s, ns, int(b), int(theta),
+                                        int(key), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, capacity: int, timeout_ms: int = -1):
+        """(blockers, latency_ms); raises IminError(code=-6) if not finished within timeout_ms."""
+        out = np.zeros(max(int(capacity), 1), dtype=np.int32)
+        cnt = ctypes.c_int32()
+        lat = ctypes.c_double()
+        _check(lib().imin_server_wait(self._h, int(ticket), int(timeout_ms),
+                                      out.ctypes.data_as(ctypes.c_void_p), int(capacity),
+                                      ctypes.byref(cnt), ctypes.byref(lat)))
+        return out[:cnt.value], lat.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().imin_server_get_stats(self._h, ctypes.byref(st)))
+        return {k: int(getattr(st, k)) for k, _ in st._fields_}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().imin_server_destroy(self._h)
+        self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 # ---- measurement hooks ---------------------------------------------------------------------

@@ -58,7 +58,7 @@ def test_batch_edge_cases_and_fallbacks(cuda_lib, monkeypatch):
         res = f(items)
         for it, r in zip(items, res):
             assert np.array_equal(r, single(*it)), (drv, it)
-        # a graph above the block tier's size makes the batch run query by query
+        # a graph above 2^18 vertices joins the batch in the global-bitmap size class
         res = f(items + [(hb, sb, 3, 500, 77)])
         assert np.array_equal(res[-1], single(hb, sb, 3, 500, 77))
     # force the batched whole-graph kernel (tiny non-tree capacity in the block tier)
