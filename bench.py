@@ -48,9 +48,12 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target CPU time of the oracle baseline sample")
-    p.add_argument("--workload", choices=("rmat17", "batch256"), default="rmat17",
+    p.add_argument("--workload", choices=("rmat17", "batch256", "serving"), default="rmat17",
                    help="rmat17: one AdvancedGreedy query on R-MAT 2^17 (the headline line); "
-                        "batch256: 256 Chung-Lu/TR queries, batched vs one query per launch")
+                        "batch256: 256 Chung-Lu/TR queries, batched vs one query per launch; "
+                        "serving: Poisson request stream on the R-MAT 2^17 and 2^22 graphs")
+    p.add_argument("--requests", type=int, default=30,
+                   help="serving: number of requests (the full configuration has 2,000)")
     return p.parse_args(argv)
 
 
@@ -299,6 +302,91 @@ def run_batch(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_serving(args, rank, world):
+    """Requests against the R-MAT 2^17 (m=2^20) and R-MAT 2^22 (m=2^26) WC graphs held resident:
+    each picks a graph with probability 1/2, |S| ~ U[10, 500], b ~ U[10, 100],
+    theta ~ U[1e4, 1e5] (AdvancedGreedy). Phase 1 submits all requests at once to measure the
+    saturation rate; phase 2 replays them with Poisson arrivals at 80 % of that rate and reports
+    p50/p99 latency and throughput; the serial baseline runs a subset one query at a time."""
+    import threading
+
+    import numpy as np
+    import torch
+    from paper_2302_13529_gb300 import build, imin, workloads as W
+
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    g17 = W.rmat17_query().graph
+    g22 = W.rmat22_query().graph
+    graphs = [g17, g22]
+    hs = [imin.load_graph(g) for g in graphs]
+    rng = np.random.default_rng(5000 + rank)
+    reqs = []
+    for i in range(args.requests):
+        gi = int(rng.integers(0, 2))
+        k = int(rng.integers(10, 501))
+        reqs.append((gi, W.uniform_seeds(graphs[gi].n, k, int(rng.integers(1 << 30))),
+                     int(rng.integers(10, 101)), int(rng.integers(10_000, 100_001)),
+                     int(rng.integers(1 << 62))))
+    samples = sum(b * t for _, _, b, t, _ in reqs)
+
+    def serve(arrivals):
+        """Submit reqs[:len(arrivals)] at the given offsets (s); return (elapsed, latencies, stats)."""
+        todo = reqs[:len(arrivals)]
+        lat = [None] * len(todo)
+        with imin.Server() as srv:
+            t0 = time.perf_counter()
+            tickets = [None] * len(todo)
+
+            def submitter():
+                for i, (gi, s, b, t, k) in enumerate(todo):
+                    wait = arrivals[i] - (time.perf_counter() - t0)
+                    if wait > 0:
+                        time.sleep(wait)
+                    tickets[i] = srv.submit(0, hs[gi], s, b, t, k)
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            th.join()
+            for i, (gi, s, b, t, k) in enumerate(todo):
+                _, lat[i] = srv.wait(tickets[i], capacity=b)
+            elapsed = time.perf_counter() - t0
+            st = srv.stats()
+        return elapsed, np.array(lat), st
+
+    serve([0.0] * min(len(reqs), 2))  # warm-up (module load, first plans)
+    burst_s, burst_lat, _ = serve([0.0] * len(reqs))
+    rate = 0.8 * len(reqs) / burst_s  # requests per second at 80 % of saturation
+    gaps = np.random.default_rng(6000 + rank).exponential(1.0 / rate, size=len(reqs))
+    poisson_s, lat, st = serve(list(np.cumsum(gaps) - gaps[0]))
+    # serial baseline: one query at a time on a subset (about a third of the requests)
+    sub_ids = list(range(0, len(reqs), 3))
+    t = time.perf_counter()
+    for i in sub_ids:
+        gi, s, b, th_, k = reqs[i]
+        imin.advanced_greedy(hs[gi], s, b, th_, k)
+    torch.cuda.synchronize()
+    serial_s = time.perf_counter() - t
+    serial_samples = sum(reqs[i][2] * reqs[i][3] for i in sub_ids)
+    line = {"metric": METRIC, "value": samples / poisson_s, "unit": "samples/s", "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * poisson_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "uint32", "data": "synthetic",
+            "config": {"workload": "serving-rmat17-rmat22-advanced-greedy",
+                       "requests": len(reqs), "full_configuration_requests": 2000,
+                       "arrivals": f"Poisson at 80% of the burst rate ({rate:.3f} req/s)",
+                       "samples": samples},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "burst": {"seconds": burst_s, "samples_per_s": samples / burst_s,
+                      "p50_ms": float(np.percentile(burst_lat, 50)),
+                      "p99_ms": float(np.percentile(burst_lat, 99))},
+            "serial_one_query_at_a_time": {"value": serial_samples / serial_s, "unit": "samples/s",
+                                           "requests": len(sub_ids)},
+            "server": st}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     rank, world, local_rank = dist_env()
@@ -317,6 +405,9 @@ def main(argv=None):
 
     if args.workload == "batch256":
         run_batch(args, rank, world, dist)
+        return
+    if args.workload == "serving":
+        run_serving(args, rank, world)
         return
     q = W.rmat17_query()
     if args.impl == "reference":
