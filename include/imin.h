@@ -232,6 +232,27 @@ int imin_estimate_decrease_stats(const imin_graph* g, const int32_t* seeds, int3
                                  uint64_t key, uint32_t round, uint64_t* out_delta,
                                  imin_stats* stats, void* stream);
 
+/* ---- autotuning (launch configuration only; the paper has no counterpart) ---------------- */
+
+/* Choose the warp/block cutoff for this graph and seed-set size and cache it in the graph handle.
+ * Samples of Alg. 2 whose cascade (non-seed reached vertices) stays within the cutoff are
+ * finished by the warp-per-sample tier; larger ones are re-run by the block-per-sample tier.
+ * After one untimed warm-up call, the tuner times one Alg. 2 call of 8,192 samples (round 0 of
+ * `key`, no blockers) for each candidate cutoff {0, 64, 96, 128, 192} (0 = block tier only) and
+ * keeps the fastest.
+ * The cutoff never changes any result of this library, only which kernel computes a sample.
+ * The estimate and greedy calls tune lazily on first use for each graph and seed-set size class
+ * (ceil(log2 n_seeds)) unless IMIN_AUTOTUNE=0 (fixed cutoff 96) or IMIN_TIER0_VERTICES=<c>
+ * (forced cutoff c); a call on a stream under capture uses 96. This entry point re-tunes
+ * unconditionally.
+ *   seeds     int32[n_seeds], host or device, distinct ids in [0, n).
+ *   key       Philox key of the timed calls.
+ *   stream    CUDA stream (NULL: legacy default); synchronized.
+ *   out_cutoff  receives the chosen cutoff.
+ * Errors: IMIN_ERR_INVALID (bad handle, seeds or NULL output), IMIN_ERR_CUDA, IMIN_ERR_NOMEM. */
+int imin_autotune(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, uint64_t key,
+                  void* stream, int32_t* out_cutoff);
+
 /* ---- measurement hooks (throughput accounting; the paper has no counterpart) ------------- */
 
 /* Work counters of the last successful estimate / greedy call on the calling thread, summed

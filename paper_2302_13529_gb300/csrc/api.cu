@@ -263,11 +263,11 @@ struct Query {
 };
 
 int setup_query(const imin_graph* g, const std::vector<int32_t>& seeds, uint32_t theta,
-                unsigned long long* out_delta_dev, Query& q)
+                unsigned long long* out_delta_dev, uint32_t cutoff, Query& q)
 {
     cudaStream_t s = q.arena.s;
     q.words = (g->n + 31) / 32;
-    q.plan = plan_tiers(g->dev, g->n, g->m, static_cast<uint32_t>(seeds.size()));
+    q.plan = plan_tiers(g->dev, g->n, g->m, static_cast<uint32_t>(seeds.size()), cutoff);
     IMIN_CUDA(q.arena.alloc(&q.seeds, seeds.size()));
     IMIN_CUDA(q.arena.alloc(&q.excl, q.words));
     if (out_delta_dev != nullptr) {
@@ -293,14 +293,14 @@ int setup_query(const imin_graph* g, const std::vector<int32_t>& seeds, uint32_t
     return IMIN_OK;
 }
 
-// One Alg. 2 call: the sample tiers in order (3 then 2 when the block-per-sample tier
-// applies, otherwise 0, 1, 2).
+// One Alg. 2 call: the sample tiers in order -- 0 (when the cutoff is not 0), 3, 2 when the
+// block-per-sample tier applies, otherwise 0, 1, 2. A tier with no blocks planned is skipped.
 cudaError_t enqueue_call(const SampleParams& P, const Query& q, CallTimer& T)
 {
     static const int kWarpOrder[] = {0, 1, 2};
-    static const int kCtaOrder[] = {kTierCta, kTierWhole};
+    static const int kCtaOrder[] = {0, kTierCta, kTierWhole};
     const int* order = q.plan.use_cta ? kCtaOrder : kWarpOrder;
-    const int count = q.plan.use_cta ? 2 : 3;
+    const int count = 3;
     for (int k = 0; k < count; ++k) {
         const int t = order[k];
         uint8_t* scr = t == 1 ? q.scratch1 : (t == 2 ? q.scratch2 : (t == kTierCta ? q.scratch3 : nullptr));
@@ -383,6 +383,111 @@ int common_checks(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, ui
     return check_ids(hseeds, g->n, mark, 1, "seeds");
 }
 
+// ---- warp/block cutoff autotuner -----------------------------------------------------------
+// Samples whose cascade stays within the cutoff (non-seed vertices) finish in the warp tier 0,
+// whose per-sample overhead is lower; bigger ones are re-run by the block tier. The best cutoff
+// depends on the graph's cascade-size distribution and on |S| (seeds take tier-0 space), so it
+// is measured: after one untimed warm-up call, one Alg. 2 call of kTuneTheta samples (round 0
+// of the caller's key, no blockers) per candidate, keeping the fastest. The choice never
+// changes a result -- only which tier computes each sample -- and is cached per graph and
+// seed-set size class.
+
+constexpr uint32_t kCutoffs[] = {0, 64, 96, 128, 192};
+constexpr uint32_t kDefaultCutoff = 96;
+constexpr uint32_t kTuneTheta = 8192;
+
+int size_class(size_t ns)
+{
+    int c = 0;
+    while (c < 31 && (size_t{1} << c) < ns) ++c;
+    return c;
+}
+
+// Device time of one Alg. 2 call (round 0, no blockers) with the given cutoff.
+int time_call(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t key, uint32_t cutoff,
+              cudaStream_t s, float* ms)
+{
+    Query q(s);
+    int rc = setup_query(g, seeds, kTuneTheta, nullptr, cutoff, q);
+    if (rc) return rc;
+    RoundCtl* ctl = nullptr;
+    IMIN_CUDA(q.arena.alloc(&ctl, 1));
+    IMIN_CUDA(cudaMemsetAsync(ctl, 0, sizeof(RoundCtl), s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    IMIN_CUDA(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        CallTimer T(s);
+        const SampleParams P = sample_params(g, q, static_cast<uint32_t>(seeds.size()), kTuneTheta, key, 0,
+                                             ctl, nullptr);
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = enqueue_call(P, q, T);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        T.collect();
+    }
+    std::vector<RoundCtl> hctl(1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hctl.data(), ctl, sizeof(RoundCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    IMIN_CUDA(e);
+    return check_ctl(hctl);
+}
+
+int tune_cutoff(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t key, cudaStream_t s,
+                uint32_t* out)
+{
+    float best = 0.f;
+    uint32_t best_c = kDefaultCutoff;
+    bool have = false;
+    int rc = time_call(g, seeds, key, kDefaultCutoff, s, &best);  // warm-up
+    if (rc) return rc;
+    for (uint32_t c : kCutoffs) {
+        float t = 0.f;
+        rc = time_call(g, seeds, key, c, s, &t);
+        if (rc) return rc;
+        if (!have || t < best) {
+            best = t;
+            best_c = c;
+            have = true;
+        }
+    }
+    *out = best_c;
+    return IMIN_OK;
+}
+
+// The cutoff for a call: IMIN_TIER0_VERTICES forces one; IMIN_AUTOTUNE=0, or a stream being
+// captured (the tuner synchronizes), gives the default; otherwise the tuned value, tuning on first
+// use for this graph and seed-set size class.
+int cutoff_for(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t key, cudaStream_t s,
+               uint32_t* out)
+{
+    if (const char* v = std::getenv("IMIN_TIER0_VERTICES"); v && *v) {
+        *out = static_cast<uint32_t>(std::strtoul(v, nullptr, 10));
+        return IMIN_OK;
+    }
+    *out = kDefaultCutoff;
+    if (const char* v = std::getenv("IMIN_AUTOTUNE"); v && *v == '0') return IMIN_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return IMIN_OK;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return IMIN_OK;
+    const int cls = size_class(seeds.size());
+    std::lock_guard<std::mutex> lk(g->tune_mu);
+    if (g->cutoff[cls] >= 0) {
+        *out = static_cast<uint32_t>(g->cutoff[cls]);
+        return IMIN_OK;
+    }
+    const int rc = tune_cutoff(g, seeds, key, s, out);
+    if (rc) return rc;
+    g->cutoff[cls] = static_cast<int32_t>(*out);
+    return IMIN_OK;
+}
+
 int estimate_impl(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
                   const int32_t* blocked, int32_t n_blocked, uint32_t theta, uint64_t key,
                   uint32_t round, uint64_t* out_delta, imin_stats* stats, void* stream)
@@ -400,8 +505,12 @@ int estimate_impl(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
     if (rc) return rc;
 
     const bool dev_out = is_device_ptr(out_delta);
+    uint32_t cutoff = 0;
+    rc = cutoff_for(g, hseeds, key, s, &cutoff);
+    if (rc) return rc;
     Query q(s);
-    rc = setup_query(g, hseeds, theta, dev_out ? reinterpret_cast<unsigned long long*>(out_delta) : nullptr, q);
+    rc = setup_query(g, hseeds, theta, dev_out ? reinterpret_cast<unsigned long long*>(out_delta) : nullptr,
+                     cutoff, q);
     if (rc) return rc;
     RoundCtl* ctl = nullptr;
     int32_t* dblocked = nullptr;
@@ -451,8 +560,11 @@ int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t
     *out_count = 0;
     if (b == 0) return IMIN_OK;
 
+    uint32_t cutoff = 0;
+    rc = cutoff_for(g, hseeds, key, s, &cutoff);
+    if (rc) return rc;
     Query q(s);
-    rc = setup_query(g, hseeds, theta, nullptr, q);
+    rc = setup_query(g, hseeds, theta, nullptr, cutoff, q);
     if (rc) return rc;
     int32_t* dB = nullptr;
     int32_t* flags = nullptr;  // [0] = done, [1] = vertex unblocked in the current round
@@ -623,7 +735,7 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         if (k == kBatchGlobalClass) global_bytes = bytes;
         else cta_bytes = std::max(cta_bytes, bytes);
     }
-    const TierPlan wp = plan_tiers(g0->dev, max_n, max_m, max_ns);
+    const TierPlan wp = plan_tiers(g0->dev, max_n, max_m, max_ns, 0);
 
     // per-query device buffers, packed into one allocation
     struct Off { uint64_t excl, cb, delta, flags; };
@@ -936,6 +1048,27 @@ int imin_estimate_decrease_stats(const imin_graph* g, const int32_t* seeds, int3
     g_err[0] = '\0';
     return estimate_impl(g, seeds, n_seeds, blocked, n_blocked, theta, key, round, out_delta,
                          stats, stream);
+}
+
+int imin_autotune(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, uint64_t key,
+                  void* stream, int32_t* out_cutoff)
+{
+    g_err[0] = '\0';
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (out_cutoff == nullptr) return fail(IMIN_ERR_INVALID, "out_cutoff is NULL");
+    std::vector<int32_t> hseeds;
+    std::vector<uint8_t> mark;
+    int rc = common_checks(g, seeds, n_seeds, 1, s, hseeds, mark);
+    if (rc) return rc;
+    uint32_t c = 0;
+    {
+        std::lock_guard<std::mutex> lk(g->tune_mu);
+        rc = tune_cutoff(g, hseeds, key, s, &c);
+        if (rc) return rc;
+        g->cutoff[size_class(hseeds.size())] = static_cast<int32_t>(c);
+    }
+    *out_cutoff = static_cast<int32_t>(c);
+    return IMIN_OK;
 }
 
 int imin_advanced_greedy(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b,

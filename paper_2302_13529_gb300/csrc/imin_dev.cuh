@@ -113,6 +113,7 @@ struct TierCfg {
     uint8_t* gscratch;      // tiers 1-2: per-warp slots
     uint64_t warp_bytes;    // bytes per slot (tier 0: shared memory per warp)
     uint32_t from_range;    // take samples [0, theta) directly (first tier that runs)
+    uint32_t next_tier;     // tier that re-runs this tier's overflowing samples
 };
 
 // Block-per-sample tier (sample_cta.cu): per-block slot layout and shared-memory sizes.
@@ -127,6 +128,7 @@ struct CtaCfg {
     uint32_t tree_words;     // shared words free after the BFS for a copy of idom and c
     uint64_t off_bm, off_gid, off_par, off_idom, off_rows, off_edges, slot_bytes;
     uint8_t* scratch;
+    uint32_t from_list;   // 1: take the samples that tier 0 handed over; 0: all of [0, theta)
 };
 
 // One query of a batch (batch.cu): its graph, seed set, masks, counters and results.

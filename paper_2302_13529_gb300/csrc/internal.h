@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <cuda_runtime.h>
 
@@ -44,6 +45,11 @@ struct imin_graph {
     int32_t* row_ptr = nullptr;  // [n+1]
     int32_t* col = nullptr;      // [m] padded to a multiple of 4 (+4)
     uint4* thr4 = nullptr;       // thresholds, same padding
+    // warp/block cutoff picked by the autotuner, per seed-set size class (ceil(log2 |S|));
+    // -1: not tuned yet
+    mutable std::mutex tune_mu;
+    mutable int32_t cutoff[32] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
+                                  -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
 };
 
 namespace imin {
@@ -60,7 +66,8 @@ struct TierPlan {
 };
 
 // Tier capacities for a graph with n vertices and m edges and a seed set of size ns.
-TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns);
+// cutoff: non-seed capacity of the warp tier 0 run in front of the block tier (0: none).
+TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns, uint32_t cutoff);
 
 // Enqueue tier `tier` of one Alg. 2 call (tier 0 takes samples [0, theta); tiers 1 and 2 take
 // the samples the previous tier could not hold). P.ctl must be zeroed and P.delta cleared

@@ -1,10 +1,13 @@
-// sample.cu -- the three sample tiers of Alg. 2 (DecreaseESComputation) and their planning.
+// sample.cu -- the warp-per-sample tiers of Alg. 2 (DecreaseESComputation) and the planning of
+// all tiers.
 //
-// Tier 0 keeps each warp's working set in shared memory and takes every sample first.
-// A sample whose cascade outgrows shared memory is re-run by tier 1 from a per-warp slot of
-// global scratch with capacity for 16K reached vertices; tier 2 holds any cascade (|R| <= n)
-// and is launched with few warps, because its slots scale with n. Work is handed out by an
-// atomic cursor per tier, so warps that draw small cascades keep pulling new samples.
+// Tier 0 keeps each warp's working set in shared memory and takes every sample first. In front
+// of the block-per-sample tier 3 its capacity is the warp/block cutoff (a few dozen to a few
+// hundred reached vertices, picked by the autotuner in api.cu) and a sample that outgrows it is
+// re-run by tier 3; without tier 3, it holds 256 vertices and hands over to tier 1, a per-warp
+// slot of global scratch with capacity for 16K reached vertices. Tier 2 holds any cascade
+// (|R| <= n) and is launched with few warps, because its slots scale with n. Work is handed out
+// by an atomic cursor per tier, so warps that draw small cascades keep pulling new samples.
 #include <algorithm>
 #include <cstdlib>
 
@@ -91,8 +94,9 @@ k_sample_tier(SampleParams P, TierCfg T)
         if (rc == kSampleOverflow) {
             if (lane == 0) {
                 if (kTier < kTierWhole) {
-                    const uint32_t pos = atomicAdd(&P.ctl->count[kTier + 1], 1u);
-                    P.lists[(kTier + 1) * P.theta + pos] = j;
+                    const uint32_t nt = T.next_tier;
+                    const uint32_t pos = atomicAdd(&P.ctl->count[nt], 1u);
+                    P.lists[nt * P.theta + pos] = j;
                 } else {
                     atomicOr(&P.ctl->error, kErrCapacity);
                 }
@@ -134,10 +138,12 @@ DeviceInfo device_info()
     return d;
 }
 
-TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns)
+TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns, uint32_t cutoff)
 {
     TierPlan p{};
-    const uint32_t r0 = env_u32("IMIN_TIER0_VERTICES", 256);    // non-seed capacity, tier 0
+    // non-seed capacity of tier 0: in front of the block tier it is the warp/block cutoff (0: no
+    // tier 0); behind the warp tiers alone it is 256
+    uint32_t r0 = env_u32("IMIN_TIER0_VERTICES", 256);
     const uint32_t r1 = env_u32("IMIN_TIER1_VERTICES", 16384);  // non-seed capacity, tier 1
     const uint32_t b1 = env_u32("IMIN_TIER1_BLOCKS_PER_SM", 2);
     const bool allow_cta = env_u32("IMIN_DISABLE_CTA_TIER", 0) == 0;
@@ -150,10 +156,11 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns)
         p.warps_per_block[kTierCta] = 4;
         // tier 2 only catches the rare samples with too many non-tree edges or levels
         t2_budget = std::min<uint64_t>(t2_budget, 1ull << 30);
+        r0 = cutoff;
     }
 
     // tier 0: shared memory
-    {
+    if (r0 > 0) {
         TierCfg& c = p.cfg[0];
         c.rcap = 1 + ns + r0;
         c.hcap = next_pow2(2ull * std::max<uint32_t>(r0, 32));  // load <= 1/2 + 32 in flight
@@ -171,7 +178,9 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_tier<0>,
                                                           kWarpsPerBlock * 32, p.smem_bytes[0]);
         }
-        p.blocks[0] = p.use_cta ? 0u : static_cast<uint32_t>(std::max(occ, 0)) * dev.sms;
+        p.blocks[0] = static_cast<uint32_t>(std::max(occ, 0)) * dev.sms;
+        c.next_tier = p.use_cta ? static_cast<uint32_t>(kTierCta) : 1u;
+        p.cta.from_list = p.use_cta && p.blocks[0] > 0 ? 1u : 0u;
     }
     // tier 1: per-warp global slot for up to r1 non-seed vertices
     {
@@ -181,6 +190,7 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns)
         c.hcap = next_pow2(2ull * std::max<uint32_t>(r, 32));
         c.hbits = log2u(c.hcap);
         c.ecap = std::max<uint32_t>(r / 4, 256);
+        c.next_tier = 2;
         c.dcap = std::min<uint32_t>(c.rcap, 1024);
         c.warp_bytes = (warp_layout(c.rcap, c.hcap, c.ecap, c.dcap, true).total + 255) & ~255ull;
         p.warps_per_block[1] = kWarpsPerBlock;

@@ -1,6 +1,7 @@
 // sample_cta.cu -- single-query launch of the block-per-sample tier of Alg. 2 (the routine is
-// in sample_cta.cuh): a persistent grid of 128-thread blocks takes samples [0, theta) from an
-// atomic cursor; a sample the block tier cannot hold is handed to the whole-graph warp tier.
+// in sample_cta.cuh): a persistent grid of 128-thread blocks takes samples from an atomic cursor
+// -- all of [0, theta), or the samples the warp tier 0 handed over when it ran first -- and a
+// sample the block tier cannot hold is handed to the whole-graph warp tier.
 #include <algorithm>
 #include <cstdlib>
 
@@ -44,8 +45,10 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_sample_cta(SampleParams P, C
         __syncthreads();
         if (tid == 0) sh.item = atomicAdd(&P.ctl->cursor[kTierCta], 1u);
         __syncthreads();
-        const uint32_t j = sh.item;
-        if (j >= P.theta) break;
+        const uint32_t total =
+            C.from_list ? *reinterpret_cast<const volatile uint32_t*>(&P.ctl->count[kTierCta]) : P.theta;
+        if (sh.item >= total) break;
+        const uint32_t j = C.from_list ? P.lists[kTierCta * P.theta + sh.item] : sh.item;
         const int rc = run_sample_cta<kSmemBitmap>(P, C, bm, dsm, sh, S, j, tid, sc, examined, live);
         if (tid == 0) {
             if (rc == kSampleOverflow) {

@@ -198,7 +198,7 @@ int imin_server::grow_plans(const std::vector<Req*>& active)
         }
     }
     if (regrow) {
-        whole = plan_tiers(dev, whole_n, whole_m, whole_ns);
+        whole = plan_tiers(dev, whole_n, whole_m, whole_ns, 0);
         if (whole_scratch) cudaFreeAsync(whole_scratch, s);
         const uint64_t bytes = whole.scratch_bytes[kTierWhole];
         if (cudaMallocAsync(&whole_scratch, bytes, s) != cudaSuccess) return IMIN_ERR_NOMEM;

@@ -89,6 +89,8 @@ def lib():
         for name in ("imin_advanced_greedy", "imin_greedy_replace"):
             getattr(L, name).argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
                                          ctypes.c_uint64, P, P, P]
+        L.imin_autotune.argtypes = [P, P, ctypes.c_int32, ctypes.c_uint64, P,
+                                    ctypes.POINTER(ctypes.c_int32)]
         for name in ("imin_batch_advanced_greedy", "imin_batch_greedy_replace"):
             getattr(L, name).argtypes = [ctypes.POINTER(Query), ctypes.c_int32, P]
         L.imin_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
@@ -203,6 +205,14 @@ def estimate_decrease_noalloc(gh: GraphHandle, seeds, blocked, theta, key, round
     _check(lib().imin_estimate_decrease_noalloc(gh.handle, s, ns, b, nb, int(theta), int(key),
                                                 int(round_), o, _stream(stream)))
     return out
+
+
+def autotune(gh: GraphHandle, seeds, key, stream=None) -> int:
+    """imin_autotune: re-tune and return the warp/block cutoff for this graph and |seeds|."""
+    s, ks, ns = _ptr(seeds, np.int32)
+    c = ctypes.c_int32()
+    _check(lib().imin_autotune(gh.handle, s, ns, int(key), _stream(stream), ctypes.byref(c)))
+    return c.value
 
 
 def _greedy(fn, gh, seeds, b, theta, key, out, stream):

@@ -84,11 +84,12 @@ def test_greedy_replace_chung_lu(cuda_lib, tiny):
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("path", ["warp-tiers", "block-tier-overflow"])
+@pytest.mark.parametrize("path", ["warp-tiers", "block-tier-overflow", "warp-then-block"])
 def test_tier_fallback_paths(cuda_lib, monkeypatch, path):
     """Tiny capacities push samples through every tier of a pipeline; results must not change.
     warp-tiers: shared-memory hash -> 16K global scratch -> whole-graph scratch;
-    block-tier-overflow: block-per-sample bitmap tier -> whole-graph scratch."""
+    block-tier-overflow: block-per-sample bitmap tier -> whole-graph scratch;
+    warp-then-block: warp tier with a 32-vertex cutoff -> block tier -> whole-graph scratch."""
     g = W.graph_rmat_wc(11, 16000, seed=5)
     seeds = W.uniform_seeds(g.n, 12, seed=6)
     want = O.decrease(g, seeds, [], 3000, 1234, 2)
@@ -98,9 +99,14 @@ def test_tier_fallback_paths(cuda_lib, monkeypatch, path):
         monkeypatch.setenv("IMIN_TIER0_VERTICES", "32")
         monkeypatch.setenv("IMIN_TIER1_VERTICES", "64")
         used = (0, 1, 2)
-    else:
+    elif path == "block-tier-overflow":
+        monkeypatch.setenv("IMIN_TIER0_VERTICES", "0")
         monkeypatch.setenv("IMIN_CTA_EDGE_CAP", "2")
         used = (3, 2)
+    else:
+        monkeypatch.setenv("IMIN_TIER0_VERTICES", "32")
+        monkeypatch.setenv("IMIN_CTA_EDGE_CAP", "2")
+        used = (0, 3, 2)
     got, st = cuda_lib.estimate_decrease(gh, seeds, [], 3000, 1234, 2, stats=True)
     assert np.array_equal(got, want)
     assert all(st["tier_samples"][t] > 0 for t in used), st
@@ -110,7 +116,44 @@ def test_tier_fallback_paths(cuda_lib, monkeypatch, path):
         monkeypatch.delenv(k, raising=False)
     got2, st2 = cuda_lib.estimate_decrease(gh, seeds, [], 3000, 1234, 2, stats=True)
     assert np.array_equal(got2, want)
-    assert st2["tier_samples"][3] == 3000  # default pipeline for n <= 2^18
+    # default pipeline for n <= 2^18: the tuned warp/block cutoff, then the block tier
+    assert st2["tier_samples"][0] + st2["tier_samples"][3] == 3000
+
+
+@pytest.mark.parametrize("cutoff", [0, 48, 96, 192, 400])
+def test_warp_block_cutoff_does_not_change_counters(cuda_lib, monkeypatch, cutoff):
+    """Every warp/block cutoff splits the samples differently between the two kernels; the
+    counters and blockers must equal the oracle's for all of them."""
+    g = W.graph_rmat_wc(12, 40000, seed=15)
+    seeds = W.uniform_seeds(g.n, 20, seed=16)
+    monkeypatch.setenv("IMIN_TIER0_VERTICES", str(cutoff))
+    gh = cuda_lib.load_graph(g)
+    got, st = cuda_lib.estimate_decrease(gh, seeds, [5, 7], 4000, 77, 4, stats=True)
+    assert np.array_equal(got, O.decrease(g, seeds, [5, 7], 4000, 77, 4))
+    assert sum(st["tier_samples"]) == 4000
+    if cutoff == 0:
+        assert st["tier_samples"][0] == 0
+    else:
+        assert st["tier_samples"][0] > 0 and st["tier_samples"][3] > 0, st
+    B = cuda_lib.advanced_greedy(gh, seeds, 3, 2000, 78)
+    assert np.array_equal(B, O.advanced_greedy(g, seeds, 3, 2000, 78))
+
+
+def test_autotune(cuda_lib, monkeypatch):
+    """imin_autotune picks one of the candidate cutoffs; later calls (which use the cached value)
+    still match the oracle; IMIN_AUTOTUNE=0 falls back to the fixed cutoff."""
+    g = W.graph_rmat_wc(12, 40000, seed=15)
+    seeds = W.uniform_seeds(g.n, 20, seed=16)
+    monkeypatch.delenv("IMIN_TIER0_VERTICES", raising=False)
+    gh = cuda_lib.load_graph(g)
+    c = cuda_lib.autotune(gh, seeds, 99)
+    assert c in (0, 64, 96, 128, 192)
+    want = O.decrease(g, seeds, [], 3000, 5, 1)
+    assert np.array_equal(cuda_lib.estimate_decrease(gh, seeds, [], 3000, 5, 1), want)
+    monkeypatch.setenv("IMIN_AUTOTUNE", "0")
+    got, st = cuda_lib.estimate_decrease(gh, seeds, [], 3000, 5, 1, stats=True)
+    assert np.array_equal(got, want)
+    assert st["tier_samples"][0] > 0
 
 
 def test_warp_tiers_match_on_full_size_round(cuda_lib, monkeypatch, rmat17):
