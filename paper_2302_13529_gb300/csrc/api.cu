@@ -393,7 +393,6 @@ int common_checks(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, ui
 // seed-set size class.
 
 constexpr uint32_t kCutoffs[] = {0, 64, 96, 128, 192};
-constexpr uint32_t kDefaultCutoff = 96;
 constexpr uint32_t kTuneTheta = 8192;
 
 int size_class(size_t ns)
@@ -736,9 +735,24 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         else cta_bytes = std::max(cta_bytes, bytes);
     }
     const TierPlan wp = plan_tiers(g0->dev, max_n, max_m, max_ns, 0);
+    // the warp tier in front: queries whose seed sets fit its shared-memory working set
+    std::vector<uint8_t> warp_q(nq, 0);
+    uint32_t warp_ns = 0;
+    const uint32_t cutoff = batch_cutoff();
+    for (int32_t i = 0; i < nq; ++i) {
+        if (cutoff > 0 && static_cast<uint32_t>(qs[i].n_seeds) <= kBatchWarpMaxSeeds) {
+            warp_q[i] = 1;
+            warp_ns = std::max<uint32_t>(warp_ns, static_cast<uint32_t>(qs[i].n_seeds));
+        }
+    }
+    TierCfg wcfg{};
+    uint32_t warp_blocks = 0;
+    uint64_t warp_smem = 0;
+    if (warp_ns == 0 || !plan_batch_warp(g0->dev, warp_ns, cutoff, &wcfg, &warp_blocks, &warp_smem))
+        std::fill(warp_q.begin(), warp_q.end(), 0);
 
     // per-query device buffers, packed into one allocation
-    struct Off { uint64_t excl, cb, delta, flags; };
+    struct Off { uint64_t excl, cb, delta, flags, done; };
     std::vector<Off> off(nq);
     std::vector<uint64_t> seed_off(nq + 1, 0), blk_off(nq + 1, 0);
     uint64_t total = 0;
@@ -751,6 +765,7 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         off[i].cb = take(gr ? 4ull * words : 0);
         off[i].delta = take(8ull * Q.graph->n);
         off[i].flags = take(8);
+        off[i].done = take(warp_q[i] ? Q.theta : 0);
         seed_off[i + 1] = seed_off[i] + static_cast<uint64_t>(Q.n_seeds);
         blk_off[i + 1] = blk_off[i] + static_cast<uint64_t>(Q.b);
         sum_theta += Q.theta;
@@ -825,26 +840,29 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         d.flags = reinterpret_cast<int32_t*>(buf + off[i].flags);
         d.start = 0;
         d.gr = gr ? 1 : 0;
+        d.done = warp_q[i] ? buf + off[i].done : nullptr;
         steps = std::max(steps, gr ? 2 * count[i] : count[i]);
     }
     IMIN_CUDA(cudaMemcpyAsync(dq, hq.data(), sizeof(BatchQuery) * nq, cudaMemcpyHostToDevice, s));
 
-    // per-step, per-class item prefixes: queries of other classes and inactive ones contribute
-    // no items
+    // per-step item prefixes: one row per size class (queries of other classes and inactive
+    // ones contribute no items) and one row, kRows - 1, for the warp tier
     const uint32_t chunk = static_cast<uint32_t>(std::max<uint64_t>(
         1, std::min<uint64_t>(64, sum_theta / (static_cast<uint64_t>(cta_blocks[0] + cta_blocks[1] +
                                                                      cta_blocks[2] + cta_blocks[3]) * 16 + 1))));
+    constexpr int kRows = kBatchClasses + 1;
     const size_t stride = static_cast<size_t>(nq) + 1;
-    std::vector<unsigned long long> hprefix(static_cast<size_t>(steps) * kBatchClasses * stride, 0);
-    std::vector<uint8_t> class_busy(static_cast<size_t>(steps) * kBatchClasses, 0);
+    std::vector<unsigned long long> hprefix(static_cast<size_t>(steps) * kRows * stride, 0);
+    std::vector<uint8_t> class_busy(static_cast<size_t>(steps) * kRows, 0);
     for (int32_t c = 0; c < steps; ++c) {
-        for (int k = 0; k < kBatchClasses; ++k) {
-            unsigned long long* pr = hprefix.data() + (static_cast<size_t>(c) * kBatchClasses + k) * stride;
+        for (int k = 0; k < kRows; ++k) {
+            unsigned long long* pr = hprefix.data() + (static_cast<size_t>(c) * kRows + k) * stride;
             for (int32_t i = 0; i < nq; ++i) {
-                const bool act = cls[i] == k && (gr ? c < 2 * count[i] : c < count[i]);
+                const bool in_row = k < kBatchClasses ? cls[i] == k : warp_q[i] != 0;
+                const bool act = in_row && (gr ? c < 2 * count[i] : c < count[i]);
                 pr[i + 1] = pr[i] + (act ? (qs[i].theta + chunk - 1) / chunk : 0);
             }
-            class_busy[static_cast<size_t>(c) * kBatchClasses + k] = pr[nq] > 0;
+            class_busy[static_cast<size_t>(c) * kRows + k] = pr[nq] > 0;
         }
     }
     unsigned long long* dprefix = nullptr;
@@ -875,11 +893,19 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         if (gr) {  // phase-2 unblocking of every GreedyReplace query at this step
             IMIN_CUDA(T.run(kKindOther, [&](bool* l) { *l = true; return launch_batch_unblock(B, rs); }));
         }
+        if (class_busy[static_cast<size_t>(c) * kRows + kBatchClasses]) {
+            BatchStep Bw = B;
+            Bw.prefix = dprefix + (static_cast<size_t>(c) * kRows + kBatchClasses) * stride;
+            IMIN_CUDA(T.run(kKindTier0, [&](bool* l) {
+                *l = true;
+                return launch_batch_warp(Bw, wcfg, warp_blocks, warp_smem, rs);
+            }));
+        }
         for (int k = 0; k < kBatchClasses; ++k) {
-            if (!class_busy[static_cast<size_t>(c) * kBatchClasses + k]) continue;
+            if (!class_busy[static_cast<size_t>(c) * kRows + k]) continue;
             BatchStep Bk = B;
             Bk.cls = static_cast<uint32_t>(k);
-            Bk.prefix = dprefix + (static_cast<size_t>(c) * kBatchClasses + k) * stride;
+            Bk.prefix = dprefix + (static_cast<size_t>(c) * kRows + k) * stride;
             IMIN_CUDA(T.run(kKindCta, [&](bool* l) {
                 *l = true;
                 return launch_batch_cta(Bk, cfg[k], cta_blocks[k], cta_smem[k],

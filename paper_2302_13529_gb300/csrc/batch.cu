@@ -1,11 +1,14 @@
 // batch.cu -- many independent queries (each with its own graph, seeds, budget, theta and key)
-// advanced together, one greedy round per step: every step is one launch of the block-per-sample
-// kernel over the samples of all queries that are still active, a launch of the whole-graph
-// warp kernel for the rare samples the block tier could not hold, and one selection launch with
-// a block per query. Work items are (query, chunk of samples) pairs handed out by one atomic
-// cursor, so uneven graphs and cascades are load-balanced across the whole GPU. Every query's
-// Philox stream and round numbering are those of the single-query drivers, so each query's
-// result is identical to running it alone.
+// advanced together, one greedy round per step: every step is one launch of the warp-per-sample
+// kernel over the samples of all active queries (each finishes the samples whose cascade stays
+// within the warp/block cutoff), one launch of the block-per-sample kernel per graph-size class
+// for the rest, a launch of the whole-graph warp kernel for the rare samples the block tier could
+// not hold, and one selection launch with a block per query. Work items are (query, chunk of
+// samples) pairs handed out by an atomic cursor per launch, so uneven graphs and cascades are
+// load-balanced across the whole GPU. Every query's Philox stream and round numbering are those
+// of the single-query drivers, so each query's result is identical to running it alone.
+#include <cstdlib>
+
 #include "internal.h"
 #include "sample_cta.cuh"
 #include "select_dev.cuh"
@@ -18,6 +21,8 @@ using namespace cta;
 using namespace sel;
 
 constexpr uint32_t kWholeWarps = 8;  // warps per block of the batched whole-graph kernel
+constexpr uint32_t kBatchWarps = 8;  // warps per block of the batched warp-tier kernel
+constexpr uint64_t kWarpStageBytes = kStageCap * sizeof(uint2);
 
 // Largest q with prefix[q] <= item (prefix[0] = 0, item < prefix[nq]).
 __device__ __forceinline__ uint32_t find_query(const unsigned long long* prefix, uint32_t nq,
@@ -121,6 +126,7 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCf
         const unsigned long long j0 = (item - B.prefix[q]) * B.chunk;
         const unsigned long long j1 = min(j0 + B.chunk, static_cast<unsigned long long>(Q.theta));
         for (unsigned long long j = j0; j < j1; ++j) {
+            if (Q.done != nullptr && Q.done[j] != 0) continue;  // the warp tier finished it
             const int rc = run_sample_cta<kSmemBitmap>(P, C, bm, dsm, sh, S, static_cast<uint32_t>(j), tid,
                                                        sc, examined, live);
             if (tid == 0) {
@@ -150,6 +156,76 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCf
         if (tid == 0 && sc.done > 0) {
             atomicAdd(st + kStSamples, sc.done);
             atomicAdd(st + kStReached, sc.reached);
+            atomicAdd(st + kStNontree, sc.nontree);
+            atomicAdd(st + kStPasses, sc.passes);
+        }
+    }
+}
+
+// The warp tier of a step: one warp per sample, working set in shared memory with the
+// warp/block cutoff as capacity, over the active queries that have a `done` array. Each
+// sample's outcome is stored in done[j] (1: counted here; 0: left to the block tier).
+__global__ void __launch_bounds__(kBatchWarps * 32, 4) k_batch_warp(BatchStep B, TierCfg T)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint8_t* mine = smem + wib * (kWarpStageBytes + T.warp_bytes);
+    uint8_t* base = mine + kWarpStageBytes;
+    const WarpLayout L = warp_layout(T.rcap, T.hcap, T.ecap, T.dcap, false);
+    WarpSpace<false> w;
+    w.stage = reinterpret_cast<uint2*>(mine);
+    w.lvl = reinterpret_cast<uint32_t*>(base + L.lvl);
+    w.hkey = reinterpret_cast<uint32_t*>(base + L.hkey);
+    w.hval = reinterpret_cast<uint32_t*>(base + L.hval);
+    w.gid = reinterpret_cast<int32_t*>(base + L.gid);
+    w.idom = reinterpret_cast<uint32_t*>(base + L.idom);
+    w.par = reinterpret_cast<uint32_t*>(base + L.par);
+    w.hslot = reinterpret_cast<uint32_t*>(base + L.hslot);
+    w.edges = reinterpret_cast<uint2*>(base + L.edges);
+    w.rcap = T.rcap;
+    w.hcap = T.hcap;
+    w.hbits = T.hbits;
+    w.ecap = T.ecap;
+    w.dcap = T.dcap;
+    for (uint32_t i = lane; i < w.hcap; i += 32) w.hkey[i] = kEmpty;
+    __syncwarp();
+
+    const unsigned long long total = B.prefix[B.nq];
+    SampleCounters sc;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(&B.ctl->warp_cursor, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= total) break;
+        const uint32_t q = find_query(B.prefix, B.nq, item);
+        const BatchQuery& Q = B.q[q];
+        int32_t pos;
+        bool ph2;
+        if (!step_active(Q, B, &pos, &ph2)) continue;
+        const SampleParams P = params_of(Q, B.step - Q.start);
+        const unsigned long long j0 = (item - B.prefix[q]) * B.chunk;
+        const unsigned long long j1 = min(j0 + B.chunk, static_cast<unsigned long long>(Q.theta));
+        for (unsigned long long j = j0; j < j1; ++j) {
+            const int rc = run_sample<false, true>(P, w, static_cast<uint32_t>(j), lane, sc);
+            if (lane == 0) {
+                Q.done[j] = rc == kSampleDone ? 1 : 0;
+                if (rc == kSampleError) atomicOr(&B.ctl->error, kErrInternal);
+            }
+        }
+    }
+    if (B.stats != nullptr) {
+        unsigned long long ex = sc.examined, lv = sc.live;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            ex += __shfl_down_sync(kFull, ex, o);
+            lv += __shfl_down_sync(kFull, lv, o);
+        }
+        if (lane == 0 && sc.done > 0) {
+            unsigned long long* st = B.stats;  // tier 0 slots
+            atomicAdd(st + kStSamples, sc.done);
+            atomicAdd(st + kStReached, sc.reached);
+            atomicAdd(st + kStExamined, ex);
+            atomicAdd(st + kStLive, lv);
             atomicAdd(st + kStNontree, sc.nontree);
             atomicAdd(st + kStPasses, sc.passes);
         }
@@ -258,6 +334,35 @@ bool plan_batch_cta(const DeviceInfo& dev, int32_t max_n, int32_t max_m, CtaCfg*
     *blocks = static_cast<uint32_t>(occ) * dev.sms;
     *scratch_bytes = c->slot_bytes * *blocks;
     return true;
+}
+
+bool plan_batch_warp(const DeviceInfo& dev, uint32_t max_ns, uint32_t cutoff, TierCfg* c, uint32_t* blocks,
+                     uint64_t* smem)
+{
+    if (cutoff == 0 || max_ns == 0 || max_ns > kBatchWarpMaxSeeds) return false;
+    tier0_cfg(max_ns, cutoff, c);
+    *smem = kBatchWarps * (kWarpStageBytes + c->warp_bytes);
+    if (*smem > dev.smem_optin) return false;
+    if (allow_max_dynamic_smem(k_batch_warp, dev) != cudaSuccess) return false;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_warp, kBatchWarps * 32, *smem);
+    if (occ <= 0) return false;
+    *blocks = static_cast<uint32_t>(occ) * dev.sms;
+    return true;
+}
+
+cudaError_t launch_batch_warp(const BatchStep& B, const TierCfg& c, uint32_t blocks, uint64_t smem,
+                              cudaStream_t s)
+{
+    k_batch_warp<<<blocks, kBatchWarps * 32, smem, s>>>(B, c);
+    return cudaGetLastError();
+}
+
+uint32_t batch_cutoff()
+{
+    if (const char* v = std::getenv("IMIN_TIER0_VERTICES"); v && *v)
+        return static_cast<uint32_t>(std::strtoul(v, nullptr, 10));
+    return kDefaultCutoff;
 }
 
 cudaError_t launch_batch_unblock(const BatchStep& B, cudaStream_t s)

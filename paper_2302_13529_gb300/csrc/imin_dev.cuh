@@ -146,6 +146,8 @@ struct BatchQuery {
     int32_t* flags;               // GreedyReplace: [0] stop flag, [1] vertex unblocked this step
     uint32_t start;               // step at which the query joined: its round is step - start
     int32_t gr;                   // 1: GreedyReplace schedule, 0: AdvancedGreedy
+    uint8_t* done;                // [theta] 1: the warp tier finished the sample in this step;
+                                  // NULL: the query's samples all go to the block tier
 };
 
 // Queries of a batch are grouped by visited-bitmap size (n <= 2^16, 2^17, 2^18 with the bitmap
@@ -165,6 +167,7 @@ struct BatchCtl {
     uint32_t over_cursor;
     uint32_t error;
     uint32_t pad;
+    unsigned long long warp_cursor;  // next (query, sample chunk) item of the warp tier
 };
 
 // One greedy step of a batch: round `step` of every query that is still active.

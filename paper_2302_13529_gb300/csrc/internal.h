@@ -66,6 +66,9 @@ struct TierPlan {
 };
 
 // Tier capacities for a graph with n vertices and m edges and a seed set of size ns.
+// Capacities and per-warp shared-memory bytes of the warp tier 0 (working set in shared memory)
+// for seed sets of up to ns vertices and r0 non-seed vertices.
+void tier0_cfg(uint32_t ns, uint32_t r0, TierCfg* c);
 // cutoff: non-seed capacity of the warp tier 0 run in front of the block tier (0: none).
 TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns, uint32_t cutoff);
 
@@ -96,6 +99,16 @@ cudaError_t launch_batch_whole(const BatchStep& B, const TierCfg& whole, uint32_
                                uint8_t* scratch, cudaStream_t s);
 cudaError_t launch_batch_select(const BatchStep& B, cudaStream_t s);
 uint32_t whole_warps_per_block();
+// The warp tier of a batch step (queries with at most kBatchWarpMaxSeeds seeds): capacities for
+// seed sets of up to max_ns vertices and `cutoff` non-seed vertices; false if it cannot run.
+constexpr uint32_t kBatchWarpMaxSeeds = 256;
+constexpr uint32_t kDefaultCutoff = 96;
+bool plan_batch_warp(const DeviceInfo& dev, uint32_t max_ns, uint32_t cutoff, TierCfg* c, uint32_t* blocks,
+                     uint64_t* smem);
+cudaError_t launch_batch_warp(const BatchStep& B, const TierCfg& c, uint32_t blocks, uint64_t smem,
+                              cudaStream_t s);
+// Warp/block cutoff of batched steps: IMIN_TIER0_VERTICES when set, else kDefaultCutoff.
+uint32_t batch_cutoff();
 
 // Selection (Alg. 3/4 argmax) -----------------------------------------------------------------
 struct SelectParams {

@@ -138,6 +138,19 @@ DeviceInfo device_info()
     return d;
 }
 
+void tier0_cfg(uint32_t ns, uint32_t r0, TierCfg* c)
+{
+    c->rcap = 1 + ns + r0;
+    c->hcap = next_pow2(2ull * std::max<uint32_t>(r0, 32));  // load <= 1/2 + 32 in flight
+    c->hbits = log2u(c->hcap);
+    c->ecap = std::max<uint32_t>(r0 / 2, 32);
+    c->dcap = 64;
+    c->warp_bytes = warp_layout(c->rcap, c->hcap, c->ecap, c->dcap, false).total;
+    c->gscratch = nullptr;
+    c->from_range = 1;
+    c->next_tier = kTierCta;
+}
+
 TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns, uint32_t cutoff)
 {
     TierPlan p{};
@@ -162,13 +175,7 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns, ui
     // tier 0: shared memory
     if (r0 > 0) {
         TierCfg& c = p.cfg[0];
-        c.rcap = 1 + ns + r0;
-        c.hcap = next_pow2(2ull * std::max<uint32_t>(r0, 32));  // load <= 1/2 + 32 in flight
-        c.hbits = log2u(c.hcap);
-        c.ecap = std::max<uint32_t>(r0 / 2, 32);
-        c.dcap = 64;
-        c.warp_bytes = warp_layout(c.rcap, c.hcap, c.ecap, c.dcap, false).total;
-        c.gscratch = nullptr;
+        tier0_cfg(ns, r0, &c);
         p.warps_per_block[0] = kWarpsPerBlock;
         p.smem_bytes[0] = kWarpsPerBlock * (kStageBytes + c.warp_bytes);
         p.scratch_bytes[0] = 0;

@@ -30,6 +30,7 @@ using Clock = std::chrono::steady_clock;
 
 constexpr int kAG = 0;
 constexpr int kGR = 1;
+constexpr int kPrefixRows = kBatchClasses + 1;  // item prefix rows: size classes, warp tier
 
 struct Req {
     uint64_t ticket = 0;
@@ -45,7 +46,8 @@ struct Req {
     int32_t count = 0;
     uint64_t bytes = 0;
     uint8_t* mem = nullptr;
-    uint64_t off_seeds = 0, off_excl = 0, off_cb = 0, off_delta = 0, off_blk = 0;
+    uint64_t off_seeds = 0, off_excl = 0, off_cb = 0, off_delta = 0, off_blk = 0, off_done = 0;
+    bool warp = false;  // its samples go to the warp tier first
     // result
     bool done = false;
     int status = IMIN_OK;
@@ -55,15 +57,17 @@ struct Req {
 
 uint64_t up16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
 
-void plan_request(Req& r)
+void plan_request(Req& r, uint32_t cutoff)
 {
     const uint64_t words = (static_cast<uint64_t>(r.g->n) + 31) / 32;
+    r.warp = cutoff > 0 && r.seeds.size() <= kBatchWarpMaxSeeds;
     uint64_t o = 0;
     r.off_seeds = o; o = up16(o + 4ull * r.seeds.size());
     r.off_excl = o;  o = up16(o + 4ull * words);
     r.off_cb = o;    o = up16(o + (r.driver == kGR ? 4ull * words : 0));
     r.off_delta = o; o = up16(o + 8ull * r.g->n);
     r.off_blk = o;   o = up16(o + 4ull * (r.b > 0 ? r.b : 1));
+    r.off_done = o;  o = up16(o + (r.warp ? r.theta : 0));
     r.bytes = o;
 }
 
@@ -92,7 +96,7 @@ struct imin_server {
     // device buffers owned by the worker
     BatchQuery* dq = nullptr;
     int32_t* dflags = nullptr;             // [max_active][2]
-    unsigned long long* dprefix = nullptr;  // [kBatchClasses][max_active + 1]
+    unsigned long long* dprefix = nullptr;  // [kPrefixRows][max_active + 1]
     BatchCtl* dctl = nullptr;
     uint32_t* dcb_count = nullptr;          // [max_active]
     uint2* dover = nullptr;
@@ -113,6 +117,13 @@ struct imin_server {
     uint32_t whole_ns = 0;
     TierPlan whole{};
     uint8_t* whole_scratch = nullptr;
+    // the warp tier, planned for the largest seed set among the requests it serves
+    uint32_t cutoff = 0;
+    uint32_t warp_ns = 0;
+    bool warp_ok = false;
+    TierCfg wcfg{};
+    uint32_t warp_blocks = 0;
+    uint64_t warp_smem = 0;
     uint32_t step = 0;
 
     void run();
@@ -196,6 +207,13 @@ int imin_server::grow_plans(const std::vector<Req*>& active)
             whole_ns = std::max<uint32_t>(whole_ns, static_cast<uint32_t>(r->seeds.size()));
             regrow = true;
         }
+    }
+    uint32_t ns_w = warp_ns;
+    for (Req* r : active)
+        if (r->warp) ns_w = std::max<uint32_t>(ns_w, static_cast<uint32_t>(r->seeds.size()));
+    if (ns_w > warp_ns) {
+        warp_ns = ns_w;
+        warp_ok = plan_batch_warp(dev, warp_ns, cutoff, &wcfg, &warp_blocks, &warp_smem);
     }
     if (regrow) {
         whole = plan_tiers(dev, whole_n, whole_m, whole_ns, 0);
@@ -300,6 +318,7 @@ void imin_server::run()
             d.flags = dflags + 2 * r->slot;
             d.start = r->start;
             d.gr = r->driver == kGR ? 1 : 0;
+            d.done = r->warp && warp_ok ? r->mem + r->off_done : nullptr;
             sum_theta += r->theta;
         }
         if (sum_theta > over_cap) {
@@ -309,15 +328,18 @@ void imin_server::run()
         }
         // one mixed schedule per slot: AdvancedGreedy is active for rounds < count, GreedyReplace
         // for rounds < 2*count until its stop flag (checked on the device)
+        // item prefixes: one row per size class, then the warp tier's row
         const uint32_t chunk = 16;
         const size_t stride = static_cast<size_t>(max_active) + 1;
-        bool class_busy[kBatchClasses] = {};
-        for (int k = 0; k < kBatchClasses; ++k) {
+        bool class_busy[kPrefixRows] = {};
+        for (int k = 0; k < kPrefixRows; ++k) {
             unsigned long long* pr = hprefix + k * stride;
             pr[0] = 0;
             for (int i = 0; i < max_active; ++i) {
                 const Req* r = slots[i];
-                const bool act = r != nullptr && r->count > 0 && batch_class(r->g->n) == k;
+                const bool in_row = r != nullptr && (k < kBatchClasses ? batch_class(r->g->n) == k
+                                                                        : r->warp && warp_ok);
+                const bool act = in_row && r->count > 0;
                 pr[i + 1] = pr[i] + (act ? (r->theta + chunk - 1) / chunk : 0);
             }
             class_busy[k] = pr[max_active] > 0;
@@ -326,7 +348,7 @@ void imin_server::run()
         for (Req* r : active) any_gr = any_gr || r->driver == kGR;
         if (!active.empty()) {
             SRV_CUDA(cudaMemcpyAsync(dq, hq, sizeof(BatchQuery) * max_active, cudaMemcpyHostToDevice, s));
-            SRV_CUDA(cudaMemcpyAsync(dprefix, hprefix, sizeof(unsigned long long) * kBatchClasses * stride,
+            SRV_CUDA(cudaMemcpyAsync(dprefix, hprefix, sizeof(unsigned long long) * kPrefixRows * stride,
                                      cudaMemcpyHostToDevice, s));
             SRV_CUDA(cudaMemsetAsync(dctl, 0, sizeof(BatchCtl), s));
             BatchStep B{};
@@ -341,6 +363,11 @@ void imin_server::run()
             B.prefix = dprefix;
             // every slot follows its own driver's schedule (BatchQuery::gr)
             if (any_gr) SRV_CUDA(launch_batch_unblock(B, s));
+            if (class_busy[kBatchClasses]) {
+                BatchStep Bw = B;
+                Bw.prefix = dprefix + kBatchClasses * stride;
+                SRV_CUDA(launch_batch_warp(Bw, wcfg, warp_blocks, warp_smem, s));
+            }
             for (int k = 0; k < kBatchClasses; ++k) {
                 if (!class_busy[k]) continue;
                 BatchStep Bk = B;
@@ -404,16 +431,17 @@ int imin_server_create(const imin_server_config* cfg, imin_server** out)
     cudaMemGetInfo(&free_b, &total_b);
     srv->budget = (cfg && cfg->memory_budget) ? cfg->memory_budget : static_cast<uint64_t>(free_b / 4);
     srv->max_active = (cfg && cfg->max_active > 0) ? cfg->max_active : 256;
+    srv->cutoff = batch_cutoff();
     srv->slots.assign(srv->max_active, nullptr);
     const size_t stride = static_cast<size_t>(srv->max_active) + 1;
     cudaError_t e = cudaStreamCreateWithFlags(&srv->s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&srv->dq, sizeof(BatchQuery) * srv->max_active);
     if (e == cudaSuccess) e = cudaMalloc(&srv->dflags, sizeof(int32_t) * 2 * srv->max_active);
-    if (e == cudaSuccess) e = cudaMalloc(&srv->dprefix, sizeof(unsigned long long) * kBatchClasses * stride);
+    if (e == cudaSuccess) e = cudaMalloc(&srv->dprefix, sizeof(unsigned long long) * kPrefixRows * stride);
     if (e == cudaSuccess) e = cudaMalloc(&srv->dctl, sizeof(BatchCtl));
     if (e == cudaSuccess) e = cudaMalloc(&srv->dcb_count, sizeof(uint32_t) * srv->max_active);
     if (e == cudaSuccess) e = cudaMallocHost(&srv->hq, sizeof(BatchQuery) * srv->max_active);
-    if (e == cudaSuccess) e = cudaMallocHost(&srv->hprefix, sizeof(unsigned long long) * kBatchClasses * stride);
+    if (e == cudaSuccess) e = cudaMallocHost(&srv->hprefix, sizeof(unsigned long long) * kPrefixRows * stride);
     if (e == cudaSuccess) e = cudaMallocHost(&srv->hflags, sizeof(int32_t) * 2 * srv->max_active);
     if (e == cudaSuccess) e = cudaMallocHost(&srv->hctl, sizeof(BatchCtl));
     if (e == cudaSuccess) e = cudaMallocHost(&srv->hcb, sizeof(uint32_t) * srv->max_active);
@@ -464,7 +492,7 @@ int imin_server_submit(imin_server* srv, int32_t driver, const imin_graph* g, co
         }
         mark[v] = 1;
     }
-    plan_request(*r);
+    plan_request(*r, srv->cutoff);
     if (r->bytes > srv->budget) {
         delete r;
         return fail_msg(IMIN_ERR_NOMEM, "the request's device state exceeds the server's memory budget");

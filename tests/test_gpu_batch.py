@@ -73,3 +73,29 @@ def test_batch_edge_cases_and_fallbacks(cuda_lib, monkeypatch):
     for a, b_ in zip(got, want):
         assert np.array_equal(a, b_)
     assert st["samples"] > 0
+
+
+@pytest.mark.parametrize("cutoff", ["0", "32", "400"])
+def test_batch_warp_block_cutoff(cuda_lib, monkeypatch, cutoff):
+    """The batched warp tier finishes the samples within the cutoff and marks them; the block
+    launches skip exactly those. Every cutoff (0 = block tier only) gives the single-query result,
+    and a query with more seeds than the warp tier holds goes to the block tier alone."""
+    qs = _queries(6, seed=23)
+    hs = [cuda_lib.load_graph(q[0]) for q in qs]
+    items = [(hh, s, b, t, k) for hh, (g, s, b, t, k) in zip(hs, qs)]
+    rp, col = W.chung_lu(3000, 20000, 2.1, seed=24)
+    gm = W.Graph(3000, rp, col, W.wc_thresholds(col, 3000))
+    hm = cuda_lib.load_graph(gm)
+    items.append((hm, W.uniform_seeds(3000, 300, 25), 3, 800, 26))  # 300 seeds > warp-tier limit
+    want = [cuda_lib.advanced_greedy(*it) for it in items]
+    monkeypatch.setenv("IMIN_TIER0_VERTICES", cutoff)
+    for f, single in ((cuda_lib.batch_advanced_greedy, None), (cuda_lib.batch_greedy_replace, cuda_lib.greedy_replace)):
+        got = f(items)
+        st = cuda_lib.last_stats()
+        ref = want if single is None else [single(*it) for it in items]
+        for i, (a, b_) in enumerate(zip(got, ref)):
+            assert np.array_equal(a, b_), (cutoff, i)
+        if cutoff == "0":
+            assert st["tier_samples"][0] == 0
+        else:
+            assert st["tier_samples"][0] > 0 and st["tier_samples"][3] > 0, st
