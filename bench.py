@@ -48,10 +48,11 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target CPU time of the oracle baseline sample")
-    p.add_argument("--workload", choices=("rmat17", "batch256", "serving"), default="rmat17",
+    p.add_argument("--workload", choices=("rmat17", "batch256", "serving", "rmat22"), default="rmat17",
                    help="rmat17: one AdvancedGreedy query on R-MAT 2^17 (the headline line); "
                         "batch256: 256 Chung-Lu/TR queries, batched vs one query per launch; "
-                        "serving: Poisson request stream on the R-MAT 2^17 and 2^22 graphs")
+                        "serving: Poisson request stream on the R-MAT 2^17 and 2^22 graphs; "
+                        "rmat22: AG and GR wall time of the large single query (R-MAT 2^22)")
     p.add_argument("--requests", type=int, default=30,
                    help="serving: number of requests (the full configuration has 2,000)")
     return p.parse_args(argv)
@@ -307,6 +308,54 @@ def run_batch(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_rmat22(args, rank, world):
+    """The large single query: R-MAT n=2^22, m=2^26, WC, |S|=200, b=200, theta=2*10^5, rounds
+    captured in one CUDA graph. One AdvancedGreedy query is the step (4*10^7 sampled graphs);
+    the warm-up is one 2-round query (module load, cutoff tuning, allocator pools). GreedyReplace
+    is timed once after it. Inputs are resident on the device."""
+    import torch
+    from paper_2302_13529_gb300 import build, imin, workloads as W
+
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.perf_counter()
+    q = W.rmat22_query()
+    gen_s = time.perf_counter() - t0
+    key = q.key + rank
+    gh = imin.load_graph(q.graph)
+    seeds_d = torch.from_numpy(q.seeds).cuda()
+    out_d = torch.empty(q.b, dtype=torch.int32, device="cuda")
+    cutoff = imin.autotune(gh, q.seeds, key)
+    imin.advanced_greedy(gh, seeds_d, 2, q.theta, key, out=out_d)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    walls = {}
+    for name, fn in (("ag", imin.advanced_greedy), ("gr", imin.greedy_replace)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(gh, seeds_d, q.b, q.theta, key, out=out_d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        walls[name] = e0.elapsed_time(e1) / 1e3
+        walls[name + "_stats"] = imin.last_stats()
+    st = walls["ag_stats"]
+    samples = st["samples"]
+    line = {"metric": METRIC, "value": samples / walls["ag"], "unit": "samples/s", "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * walls["ag"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "uint32", "data": "synthetic",
+            "config": {"workload": "rmat22-wc-advanced-greedy", "n": q.graph.n, "m": q.graph.m,
+                       "seeds": len(q.seeds), "b": q.b, "theta": q.theta,
+                       "warp_block_cutoff": cutoff, "generation_s": round(gen_s, 1),
+                       "l2": "graph (528 MB) larger than L2"},
+            "ag_wall_s": walls["ag"], "gr_wall_s": walls["gr"],
+            "gr_samples": walls["gr_stats"]["samples"],
+            "work": {"reached_per_sample": st["reached"] / samples,
+                     "examined_edges_per_sample": st["examined_edges"] / samples,
+                     "tier_samples": st["tier_samples"]}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_serving(args, rank, world):
     """Requests against the R-MAT 2^17 (m=2^20) and R-MAT 2^22 (m=2^26) WC graphs held resident:
     each picks a graph with probability 1/2, |S| ~ U[10, 500], b ~ U[10, 100],
@@ -413,6 +462,9 @@ def main(argv=None):
         return
     if args.workload == "serving":
         run_serving(args, rank, world)
+        return
+    if args.workload == "rmat22":
+        run_rmat22(args, rank, world)
         return
     q = W.rmat17_query()
     if args.impl == "reference":

@@ -387,13 +387,15 @@ int common_checks(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, ui
 // Samples whose cascade stays within the cutoff (non-seed vertices) finish in the warp tier 0,
 // whose per-sample overhead is lower; bigger ones are re-run by the block tier. The best cutoff
 // depends on the graph's cascade-size distribution and on |S| (seeds take tier-0 space), so it
-// is measured: after one untimed warm-up call, one Alg. 2 call of kTuneTheta samples (round 0
-// of the caller's key, no blockers) per candidate, keeping the fastest. The choice never
-// changes a result -- only which tier computes each sample -- and is cached per graph and
-// seed-set size class.
+// is measured: after one untimed warm-up call, kTuneReps Alg. 2 calls of kTuneTheta samples
+// (round 0 of the caller's key, no blockers) per candidate, interleaved across candidates so
+// that a clock or load change hits all of them alike; the candidate with the smallest minimum
+// time wins. The choice never changes a result -- only which tier computes each sample -- and
+// is cached per graph and seed-set size class.
 
 constexpr uint32_t kCutoffs[] = {0, 64, 96, 128, 192};
 constexpr uint32_t kTuneTheta = 8192;
+constexpr int kTuneReps = 3;
 
 int size_class(size_t ns)
 {
@@ -438,22 +440,22 @@ int time_call(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t k
 int tune_cutoff(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t key, cudaStream_t s,
                 uint32_t* out)
 {
-    float best = 0.f;
-    uint32_t best_c = kDefaultCutoff;
-    bool have = false;
-    int rc = time_call(g, seeds, key, kDefaultCutoff, s, &best);  // warm-up
+    constexpr int kCand = static_cast<int>(sizeof(kCutoffs) / sizeof(kCutoffs[0]));
+    float warm = 0.f, t[kCand];
+    int rc = time_call(g, seeds, key, kDefaultCutoff, s, &warm);  // warm-up
     if (rc) return rc;
-    for (uint32_t c : kCutoffs) {
-        float t = 0.f;
-        rc = time_call(g, seeds, key, c, s, &t);
-        if (rc) return rc;
-        if (!have || t < best) {
-            best = t;
-            best_c = c;
-            have = true;
+    for (int rep = 0; rep < kTuneReps; ++rep) {
+        for (int i = 0; i < kCand; ++i) {
+            float ms = 0.f;
+            rc = time_call(g, seeds, key, kCutoffs[i], s, &ms);
+            if (rc) return rc;
+            t[i] = rep == 0 ? ms : std::min(t[i], ms);
         }
     }
-    *out = best_c;
+    int best = 0;
+    for (int i = 1; i < kCand; ++i)
+        if (t[i] < t[best]) best = i;
+    *out = kCutoffs[best];
     return IMIN_OK;
 }
 
