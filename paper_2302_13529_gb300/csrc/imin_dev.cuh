@@ -125,7 +125,7 @@ struct CtaCfg {
     uint32_t ecap;        // non-tree edges per slot
     uint32_t global_bitmap;  // 1: the bitmap is in the slot (large n); 0: in shared memory,
                              // where it also holds the resolution hash
-    uint32_t tree_words;     // shared words free after the BFS for a copy of idom and c
+    uint32_t tree_words;     // shared words free after the BFS for the packed tree (one per vertex)
     uint64_t off_bm, off_gid, off_par, off_idom, off_rows, off_edges, slot_bytes;
     uint8_t* scratch;
     uint32_t from_list;   // 1: take the samples that tier 0 handed over; 0: all of [0, theta)

@@ -152,21 +152,14 @@ __device__ __forceinline__ void visit_staged(const SampleParams& P, const CtaCfg
     }
 }
 
-// Loads of words that other threads update with atomics (idom, c): L2 for global memory,
-// volatile for shared memory.
-template <bool G>
-__device__ __forceinline__ uint32_t ld_tree(const uint32_t* p)
-{
-    if constexpr (G) return __ldcg(p);
-    else return *reinterpret_cast<const volatile uint32_t*>(p);
-}
+// Loads of words that other threads update with atomics (idom, c): from L2.
+__device__ __forceinline__ uint32_t ld_tree(const uint32_t* p) { return __ldcg(p); }
 
 // Immediate dominators by folding NCA(idom(v), p, parent(v)) over the non-tree edges until a pass
 // changes nothing, then subtree sizes (deepest level first) and Delta += c for reached
-// non-seeds. idom and c are either shared-memory copies (G = false) or the slot arrays (G = true;
-// c then reuses the parent array, which is dead once the passes end). Returns true when the
-// iteration failed its bounds (cannot happen for a well-formed sample).
-template <bool G>
+// non-seeds, on the slot arrays in global memory, for trees too large for shared memory (c
+// reuses the parent array, which is dead once the passes end). Returns true when the iteration
+// failed its bounds (cannot happen for a well-formed sample).
 __device__ __forceinline__ bool finish_tree(const SampleParams& P, CtaShared& sh, const Slot& S,
                                             uint32_t* idom, uint32_t* c, uint32_t nR, uint32_t nE,
                                             uint32_t nlev, uint32_t ns, uint32_t tid, uint32_t* passes_out)
@@ -178,19 +171,19 @@ __device__ __forceinline__ bool finish_tree(const SampleParams& P, CtaShared& sh
             int changed = 0;
             for (uint32_t k = tid; k < nE; k += kCtaThreads) {
                 const uint2 e = S.edges[k];
-                uint32_t a = ld_tree<G>(idom + e.y), b = e.x;
+                uint32_t a = ld_tree(idom + e.y), b = e.x;
                 for (uint32_t g = 0; a != b; ++g) {
                     if (g > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = ld_tree<G>(idom + a);
-                    else b = ld_tree<G>(idom + b);
+                    if (a > b) a = ld_tree(idom + a);
+                    else b = ld_tree(idom + b);
                 }
                 b = S.par[e.y];
                 for (uint32_t g = 0; a != b; ++g) {
                     if (g > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = ld_tree<G>(idom + a);
-                    else b = ld_tree<G>(idom + b);
+                    if (a > b) a = ld_tree(idom + a);
+                    else b = ld_tree(idom + b);
                 }
-                if (!broken && a < ld_tree<G>(idom + e.y)) {
+                if (!broken && a < ld_tree(idom + e.y)) {
                     const uint32_t old = atomicMin(idom + e.y, a);
                     changed |= a < old;
                 }
@@ -206,11 +199,66 @@ __device__ __forceinline__ bool finish_tree(const SampleParams& P, CtaShared& sh
     __syncthreads();
     for (uint32_t d = nlev - 1; d >= 1; --d) {
         const uint32_t b0 = sh.lvl[d], b1 = sh.lvl[d + 1];
-        for (uint32_t i = b0 + tid; i < b1; i += kCtaThreads) atomicAdd(c + ld_tree<G>(idom + i), ld_tree<G>(c + i));
+        for (uint32_t i = b0 + tid; i < b1; i += kCtaThreads) atomicAdd(c + ld_tree(idom + i), ld_tree(c + i));
         __syncthreads();
     }
     for (uint32_t i = 1 + ns + tid; i < nR; i += kCtaThreads)
-        atomicAdd(P.delta + S.gid[i], static_cast<unsigned long long>(ld_tree<G>(c + i)));
+        atomicAdd(P.delta + S.gid[i], static_cast<unsigned long long>(ld_tree(c + i)));
+    __syncthreads();
+    return broken;
+}
+
+// finish_tree on one shared-memory word per vertex, (idom << 16) | c, for trees of fewer than
+// 2^16 local ids: c is 0 during the dominator passes, so atomicMin on the whole word is atomicMin
+// on idom; in the sweep, c < 2^16 can never carry into idom.
+__device__ __forceinline__ bool finish_tree_packed(const SampleParams& P, CtaShared& sh, const Slot& S,
+                                                   uint32_t* w, uint32_t nR, uint32_t nE, uint32_t nlev,
+                                                   uint32_t ns, uint32_t tid, uint32_t* passes_out)
+{
+    volatile uint32_t* vw = w;
+    bool broken = false;
+    uint32_t passes = 0;
+    if (nE > 0) {
+        for (;;) {
+            int changed = 0;
+            for (uint32_t k = tid; k < nE; k += kCtaThreads) {
+                const uint2 e = S.edges[k];
+                uint32_t a = vw[e.y] >> 16, b = e.x;
+                for (uint32_t g = 0; a != b; ++g) {
+                    if (g > 2 * nR) { broken = true; a = 0; break; }
+                    if (a > b) a = vw[a] >> 16;
+                    else b = vw[b] >> 16;
+                }
+                b = S.par[e.y];
+                for (uint32_t g = 0; a != b; ++g) {
+                    if (g > 2 * nR) { broken = true; a = 0; break; }
+                    if (a > b) a = vw[a] >> 16;
+                    else b = vw[b] >> 16;
+                }
+                if (!broken && a < (vw[e.y] >> 16)) {
+                    const uint32_t old = atomicMin(w + e.y, a << 16);
+                    changed |= (a << 16) < old;
+                }
+            }
+            ++passes;
+            broken = __syncthreads_or(broken);
+            if (broken || !__syncthreads_or(changed)) break;
+            if (passes > nR + 1) { broken = true; break; }
+        }
+    }
+    *passes_out = passes;
+    for (uint32_t i = tid; i < nR; i += kCtaThreads) w[i] = (vw[i] & 0xFFFF0000u) | 1u;
+    __syncthreads();
+    for (uint32_t d = nlev - 1; d >= 1; --d) {
+        const uint32_t b0 = sh.lvl[d], b1 = sh.lvl[d + 1];
+        for (uint32_t i = b0 + tid; i < b1; i += kCtaThreads) {
+            const uint32_t x = vw[i];
+            atomicAdd(w + (x >> 16), x & 0xFFFFu);
+        }
+        __syncthreads();
+    }
+    for (uint32_t i = 1 + ns + tid; i < nR; i += kCtaThreads)
+        atomicAdd(P.delta + S.gid[i], static_cast<unsigned long long>(vw[i] & 0xFFFFu));
     __syncthreads();
     return broken;
 }
@@ -399,21 +447,19 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
         if (broken) return kSampleError;
     }
 
-    // dominators, subtree sizes and counter update: on a shared-memory copy of the tree when it
-    // fits the (now free) resolution space, else on the slot arrays
+    // dominators, subtree sizes and counter update: on a packed shared-memory copy of the tree
+    // (one word per vertex) when it fits the (now free) resolution space, else on the slot arrays
     uint32_t passes = 0;
-    if (2 * nR <= C.tree_words) {
-        uint32_t* sidom = res;
-        uint32_t* sc_ = res + nR;
-        for (uint32_t i = tid; i < nR; i += kCtaThreads) sidom[i] = S.idom[i];
+    if (nR <= C.tree_words && nR < (1u << 16)) {
+        for (uint32_t i = tid; i < nR; i += kCtaThreads) res[i] = S.idom[i] << 16;
         __syncthreads();
-        broken = finish_tree<false>(P, sh, S, sidom, sc_, nR, nE, nlev, ns, tid, &passes);
+        broken = finish_tree_packed(P, sh, S, res, nR, nE, nlev, ns, tid, &passes);
         if constexpr (kResInBitmap) {
-            for (uint32_t i = tid; i < 2 * nR; i += kCtaThreads) res[i] = 0;  // it is the bitmap
+            for (uint32_t i = tid; i < nR; i += kCtaThreads) res[i] = 0;  // it is the bitmap
             __syncthreads();
         }
     } else {
-        broken = finish_tree<true>(P, sh, S, S.idom, S.par, nR, nE, nlev, ns, tid, &passes);
+        broken = finish_tree(P, sh, S, S.idom, S.par, nR, nE, nlev, ns, tid, &passes);
     }
 
     if (tid == 0) {
