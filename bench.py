@@ -572,11 +572,22 @@ def main(argv=None):
         line["clocks"] = clocks
 
     # GreedyReplace wall time (one query, device-resident inputs)
+    ag_blockers = out_d.cpu().numpy().copy()
     torch.cuda.synchronize()
     t = time.perf_counter()
     imin.greedy_replace(gh, seeds_d, q.b, q.theta, key, out=out_d)
     torch.cuda.synchronize()
     line["gr_wall_s"] = time.perf_counter() - t
+    gr_blockers = out_d.cpu().numpy().copy()
+
+    # quality of the blocker sets: expected spread by simulation (Def. 3), 10^5 sampled graphs
+    # on an independent key, as the paper evaluates its results
+    ev_key, ev_theta = (key ^ 0x5EED5EED5EED) & ((1 << 64) - 1), 100_000
+    line["expected_spread"] = {
+        "theta": ev_theta,
+        "no_blockers": imin.estimate_spread(gh, q.seeds, [], ev_theta, ev_key) / ev_theta,
+        "advanced_greedy": imin.estimate_spread(gh, q.seeds, ag_blockers, ev_theta, ev_key) / ev_theta,
+        "greedy_replace": imin.estimate_spread(gh, q.seeds, gr_blockers, ev_theta, ev_key) / ev_theta}
 
     # end to end through the C ABI from pinned host buffers
     if not args.no_e2e:

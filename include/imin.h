@@ -85,6 +85,18 @@ int imin_estimate_decrease(const imin_graph* g, const int32_t* seeds, int32_t n_
                            const int32_t* blocked, int32_t n_blocked, uint32_t theta,
                            uint64_t key, uint32_t round, uint64_t* out_delta, void* stream);
 
+/* Expected spread E(S, G[V \ B]) by simulation (Def. 3; the paper evaluates the spread of every
+ * blocker set it reports this way): out_sum = the sum over theta sampled graphs (sample j of call
+ * `round` under `key`, the same stream as Alg. 2) of the number of vertices reachable from S,
+ * seeds included. The estimate is out_sum / theta. Blocked vertices are never reached.
+ *   seeds, blocked, theta, key, round   as for imin_estimate_decrease
+ *   out_sum   host uint64: the sum
+ * Synchronizes `stream`. Errors: IMIN_ERR_INVALID, IMIN_ERR_NOMEM, IMIN_ERR_CUDA,
+ * IMIN_ERR_CAPACITY (a cascade of more than 2^18 vertices on a graph with n > 2^18). */
+int imin_estimate_spread(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
+                         const int32_t* blocked, int32_t n_blocked, uint32_t theta, uint64_t key,
+                         uint32_t round, uint64_t* out_sum, void* stream);
+
 /* AdvancedGreedy (Alg. 3): b rounds; round i (0-based) runs Alg. 2 with round index i on
  * G[V \ B] and appends the candidate of V \ (S u B) with the largest counter (strict '>' in
  * ascending vertex id, so the smallest id wins ties). Stops early only when V \ (S u B) is

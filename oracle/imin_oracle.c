@@ -33,6 +33,8 @@
  *     common positive factor 1/theta.
  *   - AdvancedGreedy (Alg. 3) and GreedyReplace (Alg. 4), argmax with strict '>' scanning
  *     candidates in ascending vertex id (so the smallest id wins ties).
+ *   - The expected spread E(S, G[V \ B]) (Def. 3) by simulation: the sum of |R| (seeds
+ *     included) over sampled graphs of the same stream.
  *
  * Philox4x32-10 is written from J. K. Salmon, M. A. Moraes, R. O. Dror, D. E. Shaw,
  * "Parallel Random Numbers: As Easy as 1, 2, 3", SC'11, Sec. 3.3 (Philox): 4 x 32-bit counter,
@@ -486,6 +488,60 @@ ORACLE_API int oracle_decrease(int32_t n, int64_t m, const int32_t *row_ptr, con
 {
     return oracle_decrease_range(n, m, row_ptr, col, thr, seeds, ns, blocked, nb, key, round, 0,
                                  theta, delta);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Expected spread by simulation (Def. 3: E(S, G) = expected number of active vertices, seeds
+ * included; the paper evaluates every blocker set it reports by simulating cascades). Sample j
+ * of call `round` is the live-edge graph of Def. 4 on the same word stream as Alg. 2; its
+ * cascade is the set of vertices reachable from the seeds over live edges without entering a
+ * blocked vertex.
+ * ---------------------------------------------------------------------------------------- */
+
+/* |R| of one sample (seeds included), by breadth-first search; s->gid is the queue. */
+static int reach_count(const graph_t *g, const int32_t *seeds, int32_t ns, uint64_t key,
+                       uint32_t round, uint32_t sample, state_t *s, int64_t *count)
+{
+    s->gid.n = 0;
+    if (iv_push(&s->gid, -1)) return -1; /* keeps local ids >= 1, as in run_sample */
+    for (int32_t i = 0; i < ns; i++) {
+        s->local[seeds[i]] = (int32_t)s->gid.n;
+        if (iv_push(&s->gid, seeds[i])) return -1;
+    }
+    for (int64_t qi = 1; qi < s->gid.n; qi++) {
+        int32_t u = s->gid.a[qi];
+        for (int64_t e = g->row_ptr[u]; e < g->row_ptr[u + 1]; e++) {
+            int32_t v = g->col[e];
+            if (s->local[v] != 0 || s->is_blocked[v]) continue;
+            if (!edge_live(key, round, sample, e, g->thr[e])) continue;
+            s->local[v] = (int32_t)s->gid.n;
+            if (iv_push(&s->gid, v)) return -1;
+        }
+    }
+    *count = s->gid.n - 1;
+    return 0;
+}
+
+/* *out_sum = sum over samples j in [j0, j1) of |R_j| (seeds included). */
+ORACLE_API int oracle_spread_range(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
+                                   const uint32_t *thr, const int32_t *seeds, int32_t ns,
+                                   const int32_t *blocked, int32_t nb, uint64_t key, uint32_t round,
+                                   uint32_t j0, uint32_t j1, uint64_t *out_sum)
+{
+    graph_t g = {n, m, row_ptr, col, thr};
+    state_t s;
+    if (state_init(&s, n)) return -1;
+    int rc = validate(&g, seeds, ns, blocked, nb, &s);
+    uint64_t total = 0;
+    for (uint32_t j = j0; !rc && j < j1; j++) {
+        int64_t c = 0;
+        rc = reach_count(&g, seeds, ns, key, round, j, &s, &c);
+        total += (uint64_t)c;
+        clear_sample(&s);
+    }
+    if (!rc) *out_sum = total;
+    state_free(&s);
+    return rc;
 }
 
 /* strict-'>' argmax over candidate vertices in ascending id; -1 if there is none */

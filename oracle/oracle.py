@@ -1,8 +1,8 @@
 """ctypes binding of the C oracle (imin_oracle.c).
 
 TEST INFRASTRUCTURE ONLY: the oracle states what the sampled-dominator-tree estimator
-(Alg. 2) and the greedy drivers AdvancedGreedy (Alg. 3) and GreedyReplace (Alg. 4) compute,
-slowly and plainly, on the CPU. Only the tests, the smoke check and the benchmark's CPU
+(Alg. 2), the greedy drivers AdvancedGreedy (Alg. 3) and GreedyReplace (Alg. 4), and the
+simulated expected spread (Def. 3) compute, slowly and plainly, on the CPU. Only the tests, the smoke check and the benchmark's CPU
 baseline use it; the product path never imports it.
 
 All functions take numpy arrays; graphs are (n, row_ptr int32[n+1], col int32[m],
@@ -67,8 +67,11 @@ def lib():
                 getattr(L, name).argtypes = g + [_i32p, ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_uint32, ctypes.c_uint64, _i32p,
                                                  ctypes.POINTER(ctypes.c_int32)]
+            L.oracle_spread_range.argtypes = g + [_i32p, ctypes.c_int32, _i32p, ctypes.c_int32,
+                                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                                  ctypes.c_uint32, _u64p]
             for name in ("oracle_sample", "oracle_decrease_range", "oracle_decrease",
-                         "oracle_advanced_greedy", "oracle_greedy_replace"):
+                         "oracle_advanced_greedy", "oracle_greedy_replace", "oracle_spread_range"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -128,6 +131,18 @@ def decrease(graph, seeds, blocked, theta, key, round_=0, j0=0) -> np.ndarray:
     _check(lib().oracle_decrease_range(n, m, rp, col, thr, s, ns, b, nb, key, round_, j0,
                                        j0 + theta, out), "decrease")
     return out[:n]
+
+
+def spread(graph, seeds, blocked, theta, key, round_=0, j0=0) -> int:
+    """Def. 3 by simulation: the sum of |R| (seeds included) over samples j0 .. j0+theta-1 of
+    call `round_` on G[V \\ B]; the expected-spread estimate is this sum / theta."""
+    n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
+    s, ns = _ids(seeds)
+    b, nb = _ids(blocked)
+    out = np.zeros(1, dtype=np.uint64)
+    _check(lib().oracle_spread_range(n, m, rp, col, thr, s, ns, b, nb, key, round_, j0,
+                                     j0 + theta, out), "spread")
+    return int(out[0])
 
 
 def advanced_greedy(graph, seeds, b, theta, key) -> np.ndarray:

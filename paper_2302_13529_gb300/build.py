@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libimin.so")
-SOURCES = ["api.cu", "sample.cu", "sample_cta.cu", "select.cu", "noalloc.cu", "batch.cu", "server.cu"]
+SOURCES = ["api.cu", "sample.cu", "sample_cta.cu", "select.cu", "noalloc.cu", "batch.cu", "server.cu",
+           "spread.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
 

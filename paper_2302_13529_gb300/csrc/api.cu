@@ -544,6 +544,64 @@ int estimate_impl(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
     return IMIN_OK;
 }
 
+// Def. 3 by simulation: out_sum = sum over theta sampled graphs of |R| (seeds included).
+int spread_impl(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, const int32_t* blocked,
+                int32_t n_blocked, uint32_t theta, uint64_t key, uint32_t round, uint64_t* out_sum,
+                void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int32_t> hseeds, hblocked;
+    std::vector<uint8_t> mark;
+    int rc = common_checks(g, seeds, n_seeds, theta, s, hseeds, mark);
+    if (rc) return rc;
+    if (out_sum == nullptr) return fail(IMIN_ERR_INVALID, "out_sum is NULL");
+    if (n_blocked < 0) return fail(IMIN_ERR_INVALID, "n_blocked must be >= 0");
+    rc = to_host(blocked, n_blocked, hblocked, s, "blocked");
+    if (rc) return rc;
+    rc = check_ids(hblocked, g->n, mark, 2, "blocked");
+    if (rc) return rc;
+
+    Query q(s);
+    rc = setup_query(g, hseeds, theta, nullptr, 0, q);
+    if (rc) return rc;
+    if (!q.plan.use_cta) return fail(IMIN_ERR_INTERNAL, "the spread kernel needs the block-per-sample tier");
+    RoundCtl* ctl = nullptr;
+    int32_t* dblocked = nullptr;
+    unsigned long long* dsum = nullptr;
+    IMIN_CUDA(q.arena.alloc(&ctl, 1));
+    IMIN_CUDA(q.arena.alloc(&dblocked, hblocked.size()));
+    IMIN_CUDA(q.arena.alloc(&dsum, 1));
+    IMIN_CUDA(cudaMemsetAsync(ctl, 0, sizeof(RoundCtl), s));
+    IMIN_CUDA(cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), s));
+    if (!hblocked.empty()) {
+        IMIN_CUDA(cudaMemcpyAsync(dblocked, hblocked.data(), sizeof(int32_t) * hblocked.size(),
+                                  cudaMemcpyHostToDevice, s));
+        IMIN_CUDA(launch_build_excl(q.excl, dblocked, n_blocked, s));
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    CallTimer T(s);
+    const SampleParams P = sample_params(g, q, static_cast<uint32_t>(n_seeds), theta, key, round, ctl, nullptr);
+    IMIN_CUDA(T.run(kKindCta, [&](bool* launched) {
+        *launched = true;
+        return launch_spread(P, q.plan.cta, q.plan.blocks[kTierCta], q.plan.smem_bytes[kTierCta], q.scratch3,
+                             dsum, s);
+    }));
+    std::vector<RoundCtl> hctl(1);
+    unsigned long long hstats[kStCount], hsum = 0;
+    IMIN_CUDA(cudaMemcpyAsync(hctl.data(), ctl, sizeof(RoundCtl), cudaMemcpyDeviceToHost, s));
+    IMIN_CUDA(cudaMemcpyAsync(hstats, q.stats, sizeof(hstats), cudaMemcpyDeviceToHost, s));
+    IMIN_CUDA(cudaMemcpyAsync(&hsum, dsum, sizeof(hsum), cudaMemcpyDeviceToHost, s));
+    IMIN_CUDA(cudaStreamSynchronize(s));
+    T.collect();
+    if (hctl[0].error & kErrCapacity)
+        return fail(IMIN_ERR_CAPACITY, "a sampled cascade exceeded the block tier's slot capacity (2^18 vertices)");
+    rc = check_ctl(hctl);
+    if (rc) return rc;
+    record_stats(hstats);
+    *out_sum = hsum;
+    return IMIN_OK;
+}
+
 enum class Driver { kAdvancedGreedy, kGreedyReplace };
 
 int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
@@ -1076,6 +1134,14 @@ int imin_estimate_decrease_stats(const imin_graph* g, const int32_t* seeds, int3
     g_err[0] = '\0';
     return estimate_impl(g, seeds, n_seeds, blocked, n_blocked, theta, key, round, out_delta,
                          stats, stream);
+}
+
+int imin_estimate_spread(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
+                         const int32_t* blocked, int32_t n_blocked, uint32_t theta, uint64_t key,
+                         uint32_t round, uint64_t* out_sum, void* stream)
+{
+    g_err[0] = '\0';
+    return spread_impl(g, seeds, n_seeds, blocked, n_blocked, theta, key, round, out_sum, stream);
 }
 
 int imin_autotune(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, uint64_t key,

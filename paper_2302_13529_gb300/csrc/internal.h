@@ -89,6 +89,11 @@ cudaError_t launch_cta_tier(const SampleParams& P, const CtaCfg& c, uint32_t blo
 // Zero the per-slot visited bitmaps of a large-graph block tier (no-op for the shared variant).
 cudaError_t prepare_cta_scratch(const CtaCfg& c, uint32_t blocks, uint8_t* scratch, cudaStream_t s);
 
+// Monte-Carlo spread (spread.cu): adds sum over samples [0, P.theta) of |R| (seeds included) to
+// *sum, with the block tier's layout `c` and `blocks` slots of `scratch`.
+cudaError_t launch_spread(const SampleParams& P, const CtaCfg& c, uint32_t blocks, uint64_t smem,
+                          uint8_t* scratch, unsigned long long* sum, cudaStream_t s);
+
 // Batched multi-query steps (batch.cu).
 bool plan_batch_cta(const DeviceInfo& dev, int32_t max_n, int32_t max_m, CtaCfg* c, uint32_t* blocks,
                     uint64_t* smem, uint64_t* scratch_bytes);

@@ -97,6 +97,8 @@ struct Slot {
 
 // Visit the staged live edges of one warp: test-and-set the visited bit of each target; a new
 // vertex gets the next local id (one shared atomic per warp), an old one yields a non-tree edge.
+// kSpread: reachability only -- no parents, dominator seeds or non-tree edges are recorded.
+template <bool kSpread>
 __device__ __forceinline__ void visit_staged(const SampleParams& P, const CtaCfg& C, uint32_t* bm,
                                              CtaShared& sh, const Slot& S, const uint2* stage,
                                              uint32_t count, uint32_t lane,
@@ -129,14 +131,17 @@ __device__ __forceinline__ void visit_staged(const SampleParams& P, const CtaCfg
                 const uint32_t lid = b + __popc(dm & lanemask_lt());
                 if (lid < C.rcap) {
                     S.gid[lid] = static_cast<int32_t>(v);
-                    S.par[lid] = ul;
-                    S.idom[lid] = ul;
+                    if constexpr (!kSpread) {
+                        S.par[lid] = ul;
+                        S.idom[lid] = ul;
+                    }
                     S.rows[lid] = row;
                 } else {
                     sh.flag = 1;
                 }
             }
         }
+        if constexpr (kSpread) continue;
         const uint32_t nm = __ballot_sync(kFull, nt);
         if (nm) {
             uint32_t b = 0;
@@ -265,7 +270,9 @@ __device__ __forceinline__ bool finish_tree_packed(const SampleParams& P, CtaSha
 
 // bm: visited bitmap (shared or global memory); res: 2 * C.res_slots words of shared memory for
 // the non-tree target resolution -- the bitmap itself when kResInBitmap (it is cleared first).
-template <bool kResInBitmap>
+// kSpread: only the BFS; |R| (seeds included) is added to sc.reached and the dominator step is
+// skipped (the Monte-Carlo spread estimate of Def. 3).
+template <bool kResInBitmap, bool kSpread = false>
 __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCfg& C, uint32_t* bm,
                                               uint32_t* res, CtaShared& sh, const Slot& S, uint32_t j,
                                               uint32_t tid, SampleCounters& sc,
@@ -377,21 +384,21 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
                 staged += __shfl_sync(kFull, cincl, 31);
                 if (staged > kStage - 32 * 4) {  // the next iteration could overflow the stage
                     __syncwarp();
-                    visit_staged(P, C, bm, sh, S, sh.stage[wid], staged, lane, lv);
+                    visit_staged<kSpread>(P, C, bm, sh, S, sh.stage[wid], staged, lane, lv);
                     __syncwarp();
                     staged = 0;
                 }
             }
             if (staged > 0) {
                 __syncwarp();
-                visit_staged(P, C, bm, sh, S, sh.stage[wid], staged, lane, lv);
+                visit_staged<kSpread>(P, C, bm, sh, S, sh.stage[wid], staged, lane, lv);
                 __syncwarp();
             }
             __syncthreads();
         }
         const uint32_t nR = *reinterpret_cast<volatile uint32_t*>(&sh.nR);
         if (*reinterpret_cast<volatile uint32_t*>(&sh.flag)) { over = true; break; }
-        if (nR > le) {
+        if (nR > le && !kSpread) {  // level offsets feed the subtree sweep only
             if (nlev + 1 > kCtaLevels) { over = true; break; }
             if (tid == 0) sh.lvl[nlev + 1] = nR;
             ++nlev;
@@ -414,6 +421,13 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
     // clear the visited bits (seeds were never marked)
     for (uint32_t i = 1 + ns + tid; i < nR; i += kCtaThreads) bm[S.gid[i] >> 5] = 0;
     __syncthreads();
+    if constexpr (kSpread) {
+        if (tid == 0) {
+            sc.reached += nR - 1;
+            sc.done += 1;
+        }
+        return kSampleDone;
+    }
 
     // non-tree edge targets: global id -> local id through a hash in the bitmap space, in
     // chunks of at most half the hash's slots

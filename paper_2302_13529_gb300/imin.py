@@ -91,6 +91,9 @@ def lib():
                                          ctypes.c_uint64, P, P, P]
         L.imin_autotune.argtypes = [P, P, ctypes.c_int32, ctypes.c_uint64, P,
                                     ctypes.POINTER(ctypes.c_int32)]
+        L.imin_estimate_spread.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_uint32,
+                                           ctypes.c_uint64, ctypes.c_uint32,
+                                           ctypes.POINTER(ctypes.c_uint64), P]
         for name in ("imin_batch_advanced_greedy", "imin_batch_greedy_replace"):
             getattr(L, name).argtypes = [ctypes.POINTER(Query), ctypes.c_int32, P]
         L.imin_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
@@ -205,6 +208,17 @@ def estimate_decrease_noalloc(gh: GraphHandle, seeds, blocked, theta, key, round
     _check(lib().imin_estimate_decrease_noalloc(gh.handle, s, ns, b, nb, int(theta), int(key),
                                                 int(round_), o, _stream(stream)))
     return out
+
+
+def estimate_spread(gh: GraphHandle, seeds, blocked, theta, key, round_=0, stream=None) -> int:
+    """imin_estimate_spread: sum over theta sampled graphs of |R| (seeds included); the expected
+    spread E(S, G[V \\ B]) is this sum divided by theta."""
+    s, ks, ns = _ptr(seeds, np.int32)
+    b, kb, nb = _ptr(blocked if blocked is not None and len(blocked) else None, np.int32)
+    out = ctypes.c_uint64()
+    _check(lib().imin_estimate_spread(gh.handle, s, ns, b, nb, int(theta), int(key), int(round_),
+                                      ctypes.byref(out), _stream(stream)))
+    return int(out.value)
 
 
 def autotune(gh: GraphHandle, seeds, key, stream=None) -> int:

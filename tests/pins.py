@@ -81,6 +81,35 @@ def exact_moments(g: Graph, seeds, blocked=(), max_uncertain=18):
     return float(spread), np.array([float(x) for x in dec]), np.array([float(x) for x in dec2])
 
 
+def exact_spread_moments(g: Graph, seeds, blocked=(), max_uncertain=18):
+    """E[|R|] and E[|R|^2] over all live-edge worlds (Def. 3 incl. seeds), exact rationals for
+    edge probabilities (thr+1)/2^32, returned as floats."""
+    seeds = list(seeds)
+    blocked = set(blocked)
+    es = edges_of(g)
+    certain = [(u, v) for (_, u, v, t) in es if t == ALWAYS]
+    unc = [(u, v, Fraction(t + 1, TWO32)) for (_, u, v, t) in es if t != ALWAYS]
+    if len(unc) > max_uncertain:
+        raise ValueError("too many uncertain edges to enumerate")
+    m1 = Fraction(0)
+    m2 = Fraction(0)
+    for bits in itertools.product((0, 1), repeat=len(unc)):
+        pw = Fraction(1)
+        live = list(certain)
+        for (u, v, p), b in zip(unc, bits):
+            if b:
+                pw *= p
+                live.append((u, v))
+            else:
+                pw *= 1 - p
+        if pw == 0:
+            continue
+        r = len(reach(g.n, live, seeds, blocked))
+        m1 += pw * r
+        m2 += pw * r * r
+    return float(m1), float(m2)
+
+
 def sample_live_edges(g: Graph, key, round_, j, word):
     """Live edges of sample j: edge e is live iff word(key, round, j, e) <= thr[e] (Def. 4)."""
     return [(u, v) for (e, u, v, t) in edges_of(g) if word(key, round_, j, e) <= t]

@@ -407,3 +407,79 @@ def test_greedy_edge_cases():
         O.decrease(g, [0, 0], [], 10, 1)  # duplicate seed
     with pytest.raises(ValueError):
         O.decrease(g, [0], [0], 10, 1)  # blocked seed
+
+
+# ------------------------------------------------------------------------------------------
+# expected spread by simulation (Def. 3)
+# ------------------------------------------------------------------------------------------
+
+def test_toy_oracle_spread_matches_paper():
+    """The simulated spread of every blocker set the paper prints for the toy graph (Ex. 1,
+    Thm. 2, Table 3) within 6 sampling standard deviations (from the exact second moment)."""
+    theta = 100_000
+    for blocked, want in TOY_SPREAD:
+        m1, m2 = pins.exact_spread_moments(TOY, [0], blocked)
+        assert abs(m1 - want) < 1e-6
+        got = O.spread(TOY, [0], blocked, theta, key=31 + len(blocked)) / theta
+        sd = math.sqrt(max(m2 - m1 * m1, 0.0) / theta)
+        assert abs(got - want) <= 6 * sd + 1e-9, (blocked, got, want, sd)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_spread_against_enumeration(seed):
+    rng = np.random.default_rng(50 + seed)
+    n = 9
+    g = W.random_small_graph(n, 15, seed=500 + seed,
+                             p_choices=(Fraction(1, 2), Fraction(1, 4), Fraction(3, 4), 1))
+    if int((g.thr != 0xFFFFFFFF).sum()) > 14:
+        pytest.skip("too many uncertain edges")
+    seeds = [int(x) for x in rng.choice(n, 2, replace=False)]
+    rest = [v for v in range(n) if v not in seeds]
+    blocked = [int(rng.choice(rest))]
+    m1, m2 = pins.exact_spread_moments(g, seeds, blocked)
+    theta = 50_000
+    got = O.spread(g, seeds, blocked, theta, key=900 + seed, round_=3) / theta
+    sd = math.sqrt(max(m2 - m1 * m1, 0.0) / theta)
+    assert abs(got - m1) <= 6 * sd + 1e-9, (got, m1, sd)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_spread_per_sample_brute_force(seed):
+    """Every sample's |R| equals an independent BFS over that sample's live edges (the edge
+    words are the KAT-pinned Philox stream), with blockers never entered."""
+    rng = np.random.default_rng(70 + seed)
+    n = int(rng.integers(10, 60))
+    g = W.random_small_graph(n, 3 * n, seed=700 + seed,
+                             p_choices=(Fraction(1, 3), Fraction(1, 2), Fraction(9, 10), 1))
+    seeds = [int(x) for x in rng.choice(n, 3, replace=False)]
+    rest = [v for v in range(n) if v not in seeds]
+    blocked = [int(x) for x in rng.choice(rest, 2, replace=False)]
+    key, rnd = 1234 + seed, 7
+    for j in range(25):
+        live = pins.sample_live_edges(g, key, rnd, j, O.edge_word)
+        want = len(pins.reach(n, live, seeds, blocked))
+        assert O.spread(g, seeds, blocked, 1, key, rnd, j0=j) == want, j
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_spread_certain_edges_closed_form(seed):
+    """p = 1 everywhere: every sample is G itself, so the spread is |S| + the number of
+    vertices reachable from S in G[V \\ B] (networkx descendants), exactly."""
+    import networkx as nx
+    rng = np.random.default_rng(90 + seed)
+    n = 40
+    g = W.random_small_graph(n, 70, seed=900 + seed, p_choices=(1,))
+    seeds = [int(x) for x in rng.choice(n, 3, replace=False)]
+    rest = [v for v in range(n) if v not in seeds]
+    blocked = [int(x) for x in rng.choice(rest, 4, replace=False)]
+    G = nx.DiGraph()
+    G.add_nodes_from(range(n))
+    for u in range(n):
+        for e in range(int(g.row_ptr[u]), int(g.row_ptr[u + 1])):
+            v = int(g.col[e])
+            if v not in blocked:
+                G.add_edge(u, v)
+    reached = set(seeds)
+    for s in seeds:
+        reached |= nx.descendants(G, s)
+    assert O.spread(g, seeds, blocked, 10, key=5) == 10 * len(reached)
