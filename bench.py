@@ -55,6 +55,10 @@ def parse_args(argv=None):
                         "rmat22: AG and GR wall time of the large single query (R-MAT 2^22)")
     p.add_argument("--requests", type=int, default=30,
                    help="serving: number of requests (the full configuration has 2,000)")
+    p.add_argument("--b", type=int, default=None,
+                   help="rmat22: budget override (smaller cases for profiling; default 200)")
+    p.add_argument("--theta", type=int, default=None,
+                   help="rmat22: samples per round override (default 2*10^5)")
     return p.parse_args(argv)
 
 
@@ -320,12 +324,16 @@ def run_rmat22(args, rank, world):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     t0 = time.perf_counter()
     q = W.rmat22_query()
+    if args.b is not None or args.theta is not None:
+        q = W.Query(q.graph, q.seeds, args.b if args.b is not None else q.b,
+                    args.theta if args.theta is not None else q.theta, q.key)
     gen_s = time.perf_counter() - t0
     key = q.key + rank
     gh = imin.load_graph(q.graph)
     seeds_d = torch.from_numpy(q.seeds).cuda()
     out_d = torch.empty(q.b, dtype=torch.int32, device="cuda")
-    cutoff = imin.autotune(gh, q.seeds, key)
+    forced = os.environ.get("IMIN_TIER0_VERTICES", "")
+    cutoff = int(forced) if forced else imin.autotune(gh, q.seeds, key)
     imin.advanced_greedy(gh, seeds_d, 2, q.theta, key, out=out_d)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -491,7 +499,9 @@ def main(argv=None):
     def step():
         imin.advanced_greedy(gh, seeds_d, q.b, q.theta, key, out=out_d)
 
-    cutoff = imin.autotune(gh, q.seeds, key)  # the warp/block cutoff the steps will use
+    # the warp/block cutoff the steps will use (IMIN_TIER0_VERTICES fixes it, e.g. for profiling)
+    forced = os.environ.get("IMIN_TIER0_VERTICES", "")
+    cutoff = int(forced) if forced else imin.autotune(gh, q.seeds, key)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()

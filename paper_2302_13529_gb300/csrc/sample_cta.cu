@@ -96,7 +96,7 @@ bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint3
         while (2 * slots * 2 <= c->bm_words) slots <<= 1;  // keys + values fit in the bitmap space
     } else {
         c->bm_words = nwords;
-        slots = 4096;  // 32 KB of shared memory for the resolution hash
+        slots = 2048;  // 16 KB of shared memory for the resolution hash (8 blocks per SM)
     }
     c->global_bitmap = smem_bitmap ? 0u : 1u;
     c->tree_words = smem_bitmap ? c->bm_words : 2 * slots;
@@ -112,6 +112,12 @@ bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint3
     if (const char* cap = std::getenv("IMIN_CTA_EDGE_CAP")) {  // test hook: force overflows
         const uint32_t v = static_cast<uint32_t>(std::strtoul(cap, nullptr, 10));
         if (v > 0) c->ecap = std::min(c->ecap, v);
+    }
+    // test and profiling hook: fewer local ids per slot on large graphs (smaller scratch; bigger
+    // cascades go to the whole-graph tier)
+    if (const char* cap = std::getenv("IMIN_CTA_VERTEX_CAP"); cap && !smem_bitmap) {
+        const uint32_t v = static_cast<uint32_t>(std::strtoul(cap, nullptr, 10));
+        if (v > 0) c->rcap = std::max<uint32_t>(std::min(c->rcap, v), 2u);
     }
     uint64_t o = 0;
     c->off_bm = o;    o = align16(o + (smem_bitmap ? 0ull : 4ull * c->bm_words));
