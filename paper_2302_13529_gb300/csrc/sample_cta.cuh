@@ -213,14 +213,26 @@ __device__ __forceinline__ bool finish_tree(const SampleParams& P, CtaShared& sh
     return broken;
 }
 
-// finish_tree on one shared-memory word per vertex, (idom << 16) | c, for trees of fewer than
-// 2^16 local ids: c is 0 during the dominator passes, so atomicMin on the whole word is atomicMin
-// on idom; in the sweep, c < 2^16 can never carry into idom.
+// finish_tree with the first K local ids -- the shallowest BFS levels, which every NCA walk ends
+// in -- held as one shared-memory word per vertex, (idom << 16) | c, and ids K..nR-1 (kSplit) in
+// the slot arrays (idom in S.idom; c in S.par, which is dead once the passes end). For trees of
+// fewer than 2^16 vertices: c is 0 in the shared words during the dominator passes, so atomicMin
+// on the whole word is atomicMin on idom, and in the sweep c < 2^16 never carries into idom.
+template <bool kSplit>
 __device__ __forceinline__ bool finish_tree_packed(const SampleParams& P, CtaShared& sh, const Slot& S,
-                                                   uint32_t* w, uint32_t nR, uint32_t nE, uint32_t nlev,
-                                                   uint32_t ns, uint32_t tid, uint32_t* passes_out)
+                                                   uint32_t* w, uint32_t K, uint32_t nR, uint32_t nE,
+                                                   uint32_t nlev, uint32_t ns, uint32_t tid,
+                                                   uint32_t* passes_out)
 {
     volatile uint32_t* vw = w;
+    auto idom_of = [&](uint32_t x) -> uint32_t {
+        if (!kSplit || x < K) return vw[x] >> 16;
+        return __ldcg(S.idom + x);
+    };
+    auto c_of = [&](uint32_t x) -> uint32_t {
+        if (!kSplit || x < K) return vw[x] & 0xFFFFu;
+        return __ldcg(S.par + x);
+    };
     bool broken = false;
     uint32_t passes = 0;
     if (nE > 0) {
@@ -228,21 +240,26 @@ __device__ __forceinline__ bool finish_tree_packed(const SampleParams& P, CtaSha
             int changed = 0;
             for (uint32_t k = tid; k < nE; k += kCtaThreads) {
                 const uint2 e = S.edges[k];
-                uint32_t a = vw[e.y] >> 16, b = e.x;
+                uint32_t a = idom_of(e.y), b = e.x;
                 for (uint32_t g = 0; a != b; ++g) {
                     if (g > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = vw[a] >> 16;
-                    else b = vw[b] >> 16;
+                    if (a > b) a = idom_of(a);
+                    else b = idom_of(b);
                 }
                 b = S.par[e.y];
                 for (uint32_t g = 0; a != b; ++g) {
                     if (g > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = vw[a] >> 16;
-                    else b = vw[b] >> 16;
+                    if (a > b) a = idom_of(a);
+                    else b = idom_of(b);
                 }
-                if (!broken && a < (vw[e.y] >> 16)) {
-                    const uint32_t old = atomicMin(w + e.y, a << 16);
-                    changed |= (a << 16) < old;
+                if (!broken && a < idom_of(e.y)) {
+                    if (!kSplit || e.y < K) {
+                        const uint32_t old = atomicMin(w + e.y, a << 16);
+                        changed |= (a << 16) < old;
+                    } else {
+                        const uint32_t old = atomicMin(S.idom + e.y, a);
+                        changed |= a < old;
+                    }
                 }
             }
             ++passes;
@@ -252,18 +269,22 @@ __device__ __forceinline__ bool finish_tree_packed(const SampleParams& P, CtaSha
         }
     }
     *passes_out = passes;
-    for (uint32_t i = tid; i < nR; i += kCtaThreads) w[i] = (vw[i] & 0xFFFF0000u) | 1u;
+    for (uint32_t i = tid; i < K; i += kCtaThreads) w[i] = (vw[i] & 0xFFFF0000u) | 1u;
+    if constexpr (kSplit) {
+        for (uint32_t i = K + tid; i < nR; i += kCtaThreads) S.par[i] = 1;
+    }
     __syncthreads();
     for (uint32_t d = nlev - 1; d >= 1; --d) {
         const uint32_t b0 = sh.lvl[d], b1 = sh.lvl[d + 1];
         for (uint32_t i = b0 + tid; i < b1; i += kCtaThreads) {
-            const uint32_t x = vw[i];
-            atomicAdd(w + (x >> 16), x & 0xFFFFu);
+            const uint32_t x = idom_of(i), ci = c_of(i);
+            if (!kSplit || x < K) atomicAdd(w + x, ci);
+            else atomicAdd(S.par + x, ci);
         }
         __syncthreads();
     }
     for (uint32_t i = 1 + ns + tid; i < nR; i += kCtaThreads)
-        atomicAdd(P.delta + S.gid[i], static_cast<unsigned long long>(vw[i] & 0xFFFFu));
+        atomicAdd(P.delta + S.gid[i], static_cast<unsigned long long>(c_of(i)));
     __syncthreads();
     return broken;
 }
@@ -461,15 +482,18 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
         if (broken) return kSampleError;
     }
 
-    // dominators, subtree sizes and counter update: on a packed shared-memory copy of the tree
-    // (one word per vertex) when it fits the (now free) resolution space, else on the slot arrays
+    // dominators, subtree sizes and counter update: the shallowest ids that fit the (now free)
+    // resolution space as packed shared-memory words, the rest on the slot arrays; trees of 2^16
+    // vertices or more entirely on the slot arrays
     uint32_t passes = 0;
-    if (nR <= C.tree_words && nR < (1u << 16)) {
-        for (uint32_t i = tid; i < nR; i += kCtaThreads) res[i] = S.idom[i] << 16;
+    if (nR < (1u << 16)) {
+        const uint32_t K = min(nR, C.tree_words);
+        for (uint32_t i = tid; i < K; i += kCtaThreads) res[i] = S.idom[i] << 16;
         __syncthreads();
-        broken = finish_tree_packed(P, sh, S, res, nR, nE, nlev, ns, tid, &passes);
+        broken = K == nR ? finish_tree_packed<false>(P, sh, S, res, K, nR, nE, nlev, ns, tid, &passes)
+                         : finish_tree_packed<true>(P, sh, S, res, K, nR, nE, nlev, ns, tid, &passes);
         if constexpr (kResInBitmap) {
-            for (uint32_t i = tid; i < nR; i += kCtaThreads) res[i] = 0;  // it is the bitmap
+            for (uint32_t i = tid; i < K; i += kCtaThreads) res[i] = 0;  // it is the bitmap
             __syncthreads();
         }
     } else {
