@@ -327,3 +327,22 @@ def test_cuda_graph_capture_matches_plain_launches(cuda_lib, tiny, monkeypatch):
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
         assert np.array_equal(g_ag, cuda_lib.advanced_greedy(gh, q.seeds, q.b, 3000, q.key))
+
+
+def test_large_graph_slot_overflow_to_whole_graph_tier(cuda_lib, monkeypatch):
+    """n = 2^19 > 2^18 with the block tier's slots capped at 64 local ids: cascades beyond the cap
+    are abandoned by the block tier and re-run by the whole-graph tier; counters still equal the
+    oracle's. The spread kernel has no fallback and reports the capacity error."""
+    g = W.graph_rmat_wc(19, 1 << 20, seed=91)
+    seeds = W.uniform_seeds(g.n, 30, 92)
+    monkeypatch.setenv("IMIN_CTA_VERTEX_CAP", "64")
+    monkeypatch.setenv("IMIN_TIER0_VERTICES", "0")
+    gh = cuda_lib.load_graph(g)
+    got, st = cuda_lib.estimate_decrease(gh, seeds, [], 1500, 95, 2, stats=True)
+    assert np.array_equal(got, O.decrease(g, seeds, [], 1500, 95, 2))
+    assert st["tier_samples"][2] > 0 and st["tier_samples"][3] > 0, st
+    with pytest.raises(cuda_lib.IminError) as ei:
+        cuda_lib.estimate_spread(gh, seeds, [], 1500, 95, 2)
+    assert ei.value.code == -4  # IMIN_ERR_CAPACITY
+    monkeypatch.delenv("IMIN_CTA_VERTEX_CAP")
+    assert cuda_lib.estimate_spread(gh, seeds, [], 1500, 95, 2) == O.spread(g, seeds, [], 1500, 95, 2)

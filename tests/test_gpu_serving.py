@@ -87,3 +87,19 @@ def test_serving_large_graph_and_errors(cuda_lib):
     assert np.array_equal(b2, cuda_lib.greedy_replace(hs, small.seeds, 4, 2000, small.key))
     assert np.array_equal(b3, cuda_lib.advanced_greedy(hs, small.seeds, 6, 200_000, 5))
     assert lat1 > 0
+
+
+def test_serving_mixes_warp_tier_and_block_only_requests(cuda_lib):
+    """A request whose seed set is too large for the warp tier (300 seeds) runs next to small ones;
+    the warp tier serves only the small ones, and every result equals the request run alone."""
+    graphs = _graphs()
+    hs = [cuda_lib.load_graph(g) for g in graphs]
+    reqs = _requests(graphs, 6, seed=77)
+    reqs.append(dict(driver=1, gi=1, seeds=W.uniform_seeds(graphs[1].n, 300, 78), b=4, theta=1500, key=79))
+    reqs.append(dict(driver=0, gi=2, seeds=W.uniform_seeds(graphs[2].n, 280, 80), b=3, theta=900, key=81))
+    want = [_alone(cuda_lib, hs, r) for r in reqs]
+    with cuda_lib.Server(max_active=16) as srv:
+        tickets = [srv.submit(r["driver"], hs[r["gi"]], r["seeds"], r["b"], r["theta"], r["key"]) for r in reqs]
+        got = [srv.wait(t, capacity=max(r["b"], 1))[0] for t, r in zip(tickets, reqs)]
+    for i, (a, b) in enumerate(zip(got, want)):
+        assert np.array_equal(a, b), (i, reqs[i]["b"], len(reqs[i]["seeds"]))
