@@ -163,10 +163,14 @@ def algorithmic_bytes(stats: dict, tier: int, n_seeds: int) -> float:
     return 8.0 * r + 4.0 * e + 4.0 * l_ + 8.0 * (r - s)
 
 
+KERNEL_SOURCES = ("sample_cta.cu", "sample_cta.cuh", "imin_dev.cuh", "internal.h")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sources that define the block-tier kernel (its translation unit and headers)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2302_13529_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 

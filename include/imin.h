@@ -249,14 +249,16 @@ int imin_estimate_decrease_stats(const imin_graph* g, const int32_t* seeds, int3
 /* Choose the warp/block cutoff for this graph and seed-set size and cache it in the graph handle.
  * Samples of Alg. 2 whose cascade (non-seed reached vertices) stays within the cutoff are
  * finished by the warp-per-sample tier; larger ones are re-run by the block-per-sample tier.
- * After one untimed warm-up call, the tuner times three Alg. 2 calls of 8,192 samples (round 0
- * of `key`, no blockers) for each candidate cutoff {0, 64, 96, 128, 192} (0 = block tier only),
- * interleaved, and keeps the candidate with the smallest minimum time.
+ * After one untimed warm-up call, the tuner times three Alg. 2 calls (round 0 of `key`, no
+ * blockers; 24 samples per resident block of the block tier, between 8,192 and 65,536) for each
+ * candidate cutoff {0, 64, 96, 128, 192} (0 = block tier only), interleaved, and keeps the
+ * candidate with the smallest minimum time.
  * The cutoff never changes any result of this library, only which kernel computes a sample.
  * The estimate and greedy calls tune lazily on first use for each graph and seed-set size class
  * (ceil(log2 n_seeds)) unless IMIN_AUTOTUNE=0 (fixed cutoff 96) or IMIN_TIER0_VERTICES=<c>
- * (forced cutoff c); a call on a stream under capture uses 96. This entry point re-tunes
- * unconditionally.
+ * (forced cutoff c); a call on a stream under capture uses 96. Results are also kept for the
+ * life of the process under a fingerprint of the graph (its sizes and sampled CSR entries), so a
+ * new handle of the same graph does not tune again. This entry point re-tunes unconditionally.
  *   seeds     int32[n_seeds], host or device, distinct ids in [0, n).
  *   key       Philox key of the timed calls.
  *   stream    CUDA stream (NULL: legacy default); synchronized.

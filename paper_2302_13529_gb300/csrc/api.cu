@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -387,15 +388,48 @@ int common_checks(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, ui
 // Samples whose cascade stays within the cutoff (non-seed vertices) finish in the warp tier 0,
 // whose per-sample overhead is lower; bigger ones are re-run by the block tier. The best cutoff
 // depends on the graph's cascade-size distribution and on |S| (seeds take tier-0 space), so it
-// is measured: after one untimed warm-up call, kTuneReps Alg. 2 calls of kTuneTheta samples
-// (round 0 of the caller's key, no blockers) per candidate, interleaved across candidates so
-// that a clock or load change hits all of them alike; the candidate with the smallest minimum
-// time wins. The choice never changes a result -- only which tier computes each sample -- and
-// is cached per graph and seed-set size class.
+// is measured: after one untimed warm-up call, kTuneReps Alg. 2 calls per candidate (round 0
+// of the caller's key, no blockers), interleaved across candidates so that a clock or load change
+// hits all of them alike; the candidate with the smallest minimum time wins. Each call samples
+// 24 graphs per resident block of the block tier (at least 8,192, at most 65,536), so that the
+// end of a call -- blocks finishing their last cascades at different times -- does not decide
+// the comparison. The choice never changes a result -- only which tier computes each sample --
+// and is cached per graph handle and seed-set size class, and process-wide under the graph's
+// fingerprint, so that a new handle of the same graph reuses it.
 
 constexpr uint32_t kCutoffs[] = {0, 64, 96, 128, 192};
-constexpr uint32_t kTuneTheta = 8192;
 constexpr int kTuneReps = 3;
+
+std::mutex g_tune_mu;
+std::map<std::pair<uint64_t, int>, int32_t> g_tuned;  // (fingerprint, size class) -> cutoff
+
+// Identity of a graph for the process-wide tuning cache: a 64-bit mix of its sizes, its device
+// and about 4,096 evenly spaced entries of each CSR array. Two different graphs that collide
+// share a cutoff, which can cost speed but never changes a result.
+uint64_t fingerprint(const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
+                     const std::vector<uint32_t>& thr, int32_t n, int64_t m, int device)
+{
+    uint64_t h = 0xcbf29ce484222325ull;
+    auto mix = [&](uint64_t x) {
+        h ^= x + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+        h *= 0x100000001b3ull;
+    };
+    mix(static_cast<uint64_t>(n));
+    mix(static_cast<uint64_t>(m));
+    mix(static_cast<uint64_t>(device));
+    const int64_t sr = std::max<int64_t>(1, (static_cast<int64_t>(n) + 1) / 4096);
+    for (int64_t i = 0; i <= n; i += sr) mix(static_cast<uint32_t>(rp[i]));
+    const int64_t se = std::max<int64_t>(1, m / 4096);
+    for (int64_t e = 0; e < m; e += se) mix((static_cast<uint64_t>(static_cast<uint32_t>(col[e])) << 32) | thr[e]);
+    return h;
+}
+
+uint32_t tune_theta(const imin_graph* g, size_t ns)
+{
+    const TierPlan p = plan_tiers(g->dev, g->n, g->m, static_cast<uint32_t>(ns), 0);
+    const uint64_t t = 24ull * std::max<uint32_t>(p.blocks[kTierCta], 1u);
+    return static_cast<uint32_t>(std::min<uint64_t>(65536, std::max<uint64_t>(8192, t)));
+}
 
 int size_class(size_t ns)
 {
@@ -406,10 +440,10 @@ int size_class(size_t ns)
 
 // Device time of one Alg. 2 call (round 0, no blockers) with the given cutoff.
 int time_call(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t key, uint32_t cutoff,
-              cudaStream_t s, float* ms)
+              uint32_t theta, cudaStream_t s, float* ms)
 {
     Query q(s);
-    int rc = setup_query(g, seeds, kTuneTheta, nullptr, cutoff, q);
+    int rc = setup_query(g, seeds, theta, nullptr, cutoff, q);
     if (rc) return rc;
     RoundCtl* ctl = nullptr;
     IMIN_CUDA(q.arena.alloc(&ctl, 1));
@@ -419,7 +453,7 @@ int time_call(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t k
     cudaError_t e = cudaEventCreate(&e1);
     if (e == cudaSuccess) {
         CallTimer T(s);
-        const SampleParams P = sample_params(g, q, static_cast<uint32_t>(seeds.size()), kTuneTheta, key, 0,
+        const SampleParams P = sample_params(g, q, static_cast<uint32_t>(seeds.size()), theta, key, 0,
                                              ctl, nullptr);
         e = cudaEventRecord(e0, s);
         if (e == cudaSuccess) e = enqueue_call(P, q, T);
@@ -442,12 +476,13 @@ int tune_cutoff(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t
 {
     constexpr int kCand = static_cast<int>(sizeof(kCutoffs) / sizeof(kCutoffs[0]));
     float warm = 0.f, t[kCand];
-    int rc = time_call(g, seeds, key, kDefaultCutoff, s, &warm);  // warm-up
+    const uint32_t theta = tune_theta(g, seeds.size());
+    int rc = time_call(g, seeds, key, kDefaultCutoff, theta, s, &warm);  // warm-up
     if (rc) return rc;
     for (int rep = 0; rep < kTuneReps; ++rep) {
         for (int i = 0; i < kCand; ++i) {
             float ms = 0.f;
-            rc = time_call(g, seeds, key, kCutoffs[i], s, &ms);
+            rc = time_call(g, seeds, key, kCutoffs[i], theta, s, &ms);
             if (rc) return rc;
             t[i] = rep == 0 ? ms : std::min(t[i], ms);
         }
@@ -483,9 +518,20 @@ int cutoff_for(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t 
         *out = static_cast<uint32_t>(g->cutoff[cls]);
         return IMIN_OK;
     }
+    {
+        std::lock_guard<std::mutex> lk2(g_tune_mu);
+        const auto it = g_tuned.find({g->fingerprint, cls});
+        if (it != g_tuned.end()) {
+            g->cutoff[cls] = it->second;
+            *out = static_cast<uint32_t>(it->second);
+            return IMIN_OK;
+        }
+    }
     const int rc = tune_cutoff(g, seeds, key, s, out);
     if (rc) return rc;
     g->cutoff[cls] = static_cast<int32_t>(*out);
+    std::lock_guard<std::mutex> lk2(g_tune_mu);
+    g_tuned[{g->fingerprint, cls}] = static_cast<int32_t>(*out);
     return IMIN_OK;
 }
 
@@ -1047,6 +1093,7 @@ int imin_load_graph(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t*
     g->dev = device_info();
     g->n = n;
     g->m = static_cast<int32_t>(m);
+    g->fingerprint = fingerprint(hrp, hcol, hthr, n, m, g->device);
     keep_pool_memory(g->device);
     const int64_t m4 = ((m + 3) / 4) * 4 + 4;  // padded so the last 16-byte group is in bounds
     hcol.resize(m4, 0);
@@ -1160,6 +1207,8 @@ int imin_autotune(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, ui
         rc = tune_cutoff(g, hseeds, key, s, &c);
         if (rc) return rc;
         g->cutoff[size_class(hseeds.size())] = static_cast<int32_t>(c);
+        std::lock_guard<std::mutex> lk2(g_tune_mu);
+        g_tuned[{g->fingerprint, size_class(hseeds.size())}] = static_cast<int32_t>(c);
     }
     *out_cutoff = static_cast<int32_t>(c);
     return IMIN_OK;

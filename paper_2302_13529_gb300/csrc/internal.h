@@ -45,6 +45,8 @@ struct imin_graph {
     int32_t* row_ptr = nullptr;  // [n+1]
     int32_t* col = nullptr;      // [m] padded to a multiple of 4 (+4)
     uint4* thr4 = nullptr;       // thresholds, same padding
+    // sampled hash of the CSR: handles of the same graph share tuning results
+    uint64_t fingerprint = 0;
     // warp/block cutoff picked by the autotuner, per seed-set size class (ceil(log2 |S|));
     // -1: not tuned yet
     mutable std::mutex tune_mu;
