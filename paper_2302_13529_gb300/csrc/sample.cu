@@ -143,8 +143,8 @@ void tier0_cfg(uint32_t ns, uint32_t r0, TierCfg* c)
     c->rcap = 1 + ns + r0;
     c->hcap = next_pow2(2ull * std::max<uint32_t>(r0, 32));  // load <= 1/2 + 32 in flight
     c->hbits = log2u(c->hcap);
-    c->ecap = std::max<uint32_t>(r0 / 2, 32);
-    c->dcap = 64;
+    c->ecap = std::max<uint32_t>(r0 / 4, 32);  // a cascade with more goes to the next tier
+    c->dcap = 32;
     c->warp_bytes = warp_layout(c->rcap, c->hcap, c->ecap, c->dcap, false).total;
     c->gscratch = nullptr;
     c->from_range = 1;
