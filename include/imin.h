@@ -249,10 +249,13 @@ int imin_estimate_decrease_stats(const imin_graph* g, const int32_t* seeds, int3
 /* Choose the warp/block cutoff for this graph and seed-set size and cache it in the graph handle.
  * Samples of Alg. 2 whose cascade (non-seed reached vertices) stays within the cutoff are
  * finished by the warp-per-sample tier; larger ones are re-run by the block-per-sample tier.
- * After one untimed warm-up call, the tuner times three Alg. 2 calls (round 0 of `key`, no
- * blockers; 24 samples per resident block of the block tier, between 8,192 and 65,536) for each
- * candidate cutoff {0, 64, 96, 128, 192} (0 = block tier only), interleaved, and keeps the
- * candidate with the smallest minimum time.
+ * After untimed warm-up calls that estimate the time per sample, the tuner times three Alg. 2
+ * calls (round 0 of `key`, no blockers; each sized to take about 2 ms, at most 24 samples per
+ * resident block of the block tier and at most 65,536) for each candidate cutoff
+ * {0, 64, 96, 128, 192} (0 = block tier only), interleaved, and keeps the candidate with the
+ * smallest minimum time. When fewer than 4 samples per block fit in 2 ms (huge cascades), it keeps
+ * 96 without timing. The first warm-up call samples at most 1,024 graphs (at most the caller's
+ * theta for the lazy tuning).
  * The cutoff never changes any result of this library, only which kernel computes a sample.
  * The estimate and greedy calls tune lazily on first use for each graph and seed-set size class
  * (ceil(log2 n_seeds)) unless IMIN_AUTOTUNE=0 (fixed cutoff 96) or IMIN_TIER0_VERTICES=<c>

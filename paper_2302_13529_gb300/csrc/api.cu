@@ -393,12 +393,17 @@ int common_checks(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, ui
 // hits all of them alike; the candidate with the smallest minimum time wins. Each call samples
 // 24 graphs per resident block of the block tier (at least 8,192, at most 65,536), so that the
 // end of a call -- blocks finishing their last cascades at different times -- does not decide
-// the comparison. The choice never changes a result -- only which tier computes each sample --
-// and is cached per graph handle and seed-set size class, and process-wide under the graph's
-// fingerprint, so that a new handle of the same graph reuses it.
+// the comparison. The cost is bounded: the warm-up call samples at most as many graphs as the
+// caller asked for (and at most 1,024); from its time per sample, each timed call is sized to
+// take about kTuneCallMs, and when fewer than 4 samples per block would fit in that time (graphs
+// whose cascades are huge, where the cutoff hardly matters) the default is kept untimed. The
+// choice never changes a result -- only which tier computes each sample -- and is cached per
+// graph handle and seed-set size class, and process-wide under the graph's fingerprint, so that
+// a new handle of the same graph reuses it.
 
 constexpr uint32_t kCutoffs[] = {0, 64, 96, 128, 192};
 constexpr int kTuneReps = 3;
+constexpr float kTuneCallMs = 2.0f;
 
 std::mutex g_tune_mu;
 std::map<std::pair<uint64_t, int>, int32_t> g_tuned;  // (fingerprint, size class) -> cutoff
@@ -424,11 +429,10 @@ uint64_t fingerprint(const std::vector<int32_t>& rp, const std::vector<int32_t>&
     return h;
 }
 
-uint32_t tune_theta(const imin_graph* g, size_t ns)
+uint32_t cta_blocks(const imin_graph* g, size_t ns)
 {
     const TierPlan p = plan_tiers(g->dev, g->n, g->m, static_cast<uint32_t>(ns), 0);
-    const uint64_t t = 24ull * std::max<uint32_t>(p.blocks[kTierCta], 1u);
-    return static_cast<uint32_t>(std::min<uint64_t>(65536, std::max<uint64_t>(8192, t)));
+    return std::max<uint32_t>(p.blocks[kTierCta], 1u);
 }
 
 int size_class(size_t ns)
@@ -471,14 +475,28 @@ int time_call(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t k
     return check_ctl(hctl);
 }
 
+// theta_hint: the caller's samples per call (0: unknown), which bounds the warm-up call.
 int tune_cutoff(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t key, cudaStream_t s,
-                uint32_t* out)
+                uint32_t theta_hint, uint32_t* out)
 {
     constexpr int kCand = static_cast<int>(sizeof(kCutoffs) / sizeof(kCutoffs[0]));
     float warm = 0.f, t[kCand];
-    const uint32_t theta = tune_theta(g, seeds.size());
-    int rc = time_call(g, seeds, key, kDefaultCutoff, theta, s, &warm);  // warm-up
+    const uint32_t blocks = cta_blocks(g, seeds.size());
+    const uint32_t tw = std::max<uint32_t>(1, std::min<uint32_t>(1024, theta_hint ? theta_hint : 1024));
+    int rc = time_call(g, seeds, key, kDefaultCutoff, tw, s, &warm);  // warm-up and cost estimate
     if (rc) return rc;
+    double per_sample = std::max(1e-7, static_cast<double>(warm) / tw);  // ms
+    if (kTuneCallMs / per_sample < 4.0 * blocks) {  // too costly to compare: keep the default
+        *out = kDefaultCutoff;
+        return IMIN_OK;
+    }
+    // a small warm-up is dominated by its slowest block; re-estimate on a call of the planned size
+    uint32_t theta = static_cast<uint32_t>(std::min<double>({kTuneCallMs / per_sample, 24.0 * blocks, 65536.0}));
+    rc = time_call(g, seeds, key, kDefaultCutoff, theta, s, &warm);
+    if (rc) return rc;
+    per_sample = std::max(1e-7, static_cast<double>(warm) / theta);
+    theta = static_cast<uint32_t>(std::min<double>({std::max(kTuneCallMs / per_sample, 4.0 * blocks),
+                                                    24.0 * blocks, 65536.0}));
     for (int rep = 0; rep < kTuneReps; ++rep) {
         for (int i = 0; i < kCand; ++i) {
             float ms = 0.f;
@@ -497,8 +515,8 @@ int tune_cutoff(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t
 // The cutoff for a call: IMIN_TIER0_VERTICES forces one; IMIN_AUTOTUNE=0, or a stream being
 // captured (the tuner synchronizes), gives the default; otherwise the tuned value, tuning on first
 // use for this graph and seed-set size class.
-int cutoff_for(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t key, cudaStream_t s,
-               uint32_t* out)
+int cutoff_for(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t key, uint32_t theta_hint,
+               cudaStream_t s, uint32_t* out)
 {
     if (const char* v = std::getenv("IMIN_TIER0_VERTICES"); v && *v) {
         *out = static_cast<uint32_t>(std::strtoul(v, nullptr, 10));
@@ -527,7 +545,7 @@ int cutoff_for(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t 
             return IMIN_OK;
         }
     }
-    const int rc = tune_cutoff(g, seeds, key, s, out);
+    const int rc = tune_cutoff(g, seeds, key, s, theta_hint, out);
     if (rc) return rc;
     g->cutoff[cls] = static_cast<int32_t>(*out);
     std::lock_guard<std::mutex> lk2(g_tune_mu);
@@ -553,7 +571,7 @@ int estimate_impl(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
 
     const bool dev_out = is_device_ptr(out_delta);
     uint32_t cutoff = 0;
-    rc = cutoff_for(g, hseeds, key, s, &cutoff);
+    rc = cutoff_for(g, hseeds, key, theta, s, &cutoff);
     if (rc) return rc;
     Query q(s);
     rc = setup_query(g, hseeds, theta, dev_out ? reinterpret_cast<unsigned long long*>(out_delta) : nullptr,
@@ -666,7 +684,7 @@ int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t
     if (b == 0) return IMIN_OK;
 
     uint32_t cutoff = 0;
-    rc = cutoff_for(g, hseeds, key, s, &cutoff);
+    rc = cutoff_for(g, hseeds, key, theta, s, &cutoff);
     if (rc) return rc;
     Query q(s);
     rc = setup_query(g, hseeds, theta, nullptr, cutoff, q);
@@ -1204,7 +1222,7 @@ int imin_autotune(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, ui
     uint32_t c = 0;
     {
         std::lock_guard<std::mutex> lk(g->tune_mu);
-        rc = tune_cutoff(g, hseeds, key, s, &c);
+        rc = tune_cutoff(g, hseeds, key, s, 0, &c);
         if (rc) return rc;
         g->cutoff[size_class(hseeds.size())] = static_cast<int32_t>(c);
         std::lock_guard<std::mutex> lk2(g_tune_mu);
