@@ -346,3 +346,37 @@ def test_large_graph_slot_overflow_to_whole_graph_tier(cuda_lib, monkeypatch):
     assert ei.value.code == -4  # IMIN_ERR_CAPACITY
     monkeypatch.delenv("IMIN_CTA_VERTEX_CAP")
     assert cuda_lib.estimate_spread(gh, seeds, [], 1500, 95, 2) == O.spread(g, seeds, [], 1500, 95, 2)
+
+
+def test_trivalency_rmat_counters_and_greedy_replace(cuda_lib):
+    """TR probabilities {0.1, 0.01, 0.001} on an R-MAT 2^13 graph (the single-query path is
+    otherwise tested mostly on WC): an Alg. 2 call with a ragged theta, and a full GreedyReplace,
+    against the oracle."""
+    rp, col = W.rmat(13, 1 << 17, W.RMAT_ABCD, 31)
+    g = W.Graph(1 << 13, rp, col, W.tr_thresholds(len(col), 32))
+    seeds = W.uniform_seeds(g.n, 25, 33)
+    gh = cuda_lib.load_graph(g)
+    got = cuda_lib.estimate_decrease(gh, seeds, [7, 11], 2001, 34, 5)
+    assert np.array_equal(got, O.decrease(g, seeds, [7, 11], 2001, 34, 5))
+    B = cuda_lib.greedy_replace(gh, seeds, 4, 500, 35)
+    assert np.array_equal(B, O.greedy_replace(g, seeds, 4, 500, 35))
+
+
+def test_tuning_is_shared_by_handles_of_one_graph(cuda_lib, monkeypatch):
+    """The warp/block cutoff is tuned once per graph and seed-set size class: a second handle of
+    the same graph launches only the kernels of its own call (no tuning calls), and both handles
+    give the oracle's counters."""
+    monkeypatch.delenv("IMIN_TIER0_VERTICES", raising=False)
+    monkeypatch.delenv("IMIN_AUTOTUNE", raising=False)
+    g = W.graph_rmat_wc(12, 40000, seed=41)
+    seeds = W.uniform_seeds(g.n, 20, seed=42)
+    want = O.decrease(g, seeds, [], 2000, 43, 1)
+    h1 = cuda_lib.load_graph(g)
+    c0 = cuda_lib.launch_count()
+    assert np.array_equal(cuda_lib.estimate_decrease(h1, seeds, [], 2000, 43, 1), want)
+    first = cuda_lib.launch_count() - c0
+    h2 = cuda_lib.load_graph(g)
+    c0 = cuda_lib.launch_count()
+    assert np.array_equal(cuda_lib.estimate_decrease(h2, seeds, [], 2000, 43, 1), want)
+    second = cuda_lib.launch_count() - c0
+    assert second < first and second <= 6, (first, second)
