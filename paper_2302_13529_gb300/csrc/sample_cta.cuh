@@ -51,24 +51,6 @@ struct CtaShared {
     uint32_t item, nR, nE, flag;
 };
 
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t tid, CtaShared& sh,
-                                                    uint32_t* total)
-{
-    const uint32_t lane = tid & 31, wid = tid >> 5;
-    const uint32_t incl = warp_incl_scan(x, lane);
-    if (lane == 31) sh.wsum[wid] = incl;
-    __syncthreads();
-    uint32_t off = 0, tot = 0;
-#pragma unroll
-    for (uint32_t w = 0; w < kCtaWarps; ++w) {
-        const uint32_t s = sh.wsum[w];
-        if (w < wid) off += s;
-        tot += s;
-    }
-    *total = tot;
-    return incl - x + off;
-}
-
 // Find-or-insert of a global id in the resolution hash (keys then values, h slots each).
 __device__ __forceinline__ uint32_t res_slot(uint32_t* keys, uint32_t hmask, uint32_t hshift,
                                              uint32_t v, bool insert)
@@ -343,8 +325,10 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
                             : 0u;
                 sum += ng[k];
             }
-            uint32_t total;
-            uint32_t run = block_excl_scan(sum, tid, sh, &total);
+            // warp-local inclusive group counts; the warps' totals locate a group's warp first,
+            // so one barrier serves the whole chunk
+            const uint32_t wincl = warp_incl_scan(sum, lane);
+            uint32_t run = wincl - sum;
 #pragma unroll
             for (uint32_t k = 0; k < kVpt; ++k) {
                 run += ng[k];
@@ -352,7 +336,11 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
                 sh.beg[tid * kVpt + k] = beg[k];
                 sh.end[tid * kVpt + k] = end[k];
             }
+            if (lane == 31) sh.wsum[wid] = wincl;
             __syncthreads();
+            static_assert(kCtaWarps == 4, "the warp offsets below assume 4 warps");
+            const uint32_t off1 = sh.wsum[0], off2 = off1 + sh.wsum[1], off3 = off2 + sh.wsum[2];
+            const uint32_t total = off3 + sh.wsum[3];
 
             // ---- groups: one per thread per iteration; live edges accumulate in the warp's
             // stage, which is visited by the full warp whenever it is at least half full and
@@ -367,14 +355,17 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
                 nob = 0;
                 noe = 0;
                 if (t < total) {
-                    uint32_t p = 0;
+                    // the owner's warp, then the owner within the warp's kVpt * 32 entries
+                    const uint32_t w = (t >= off1 ? 1u : 0u) + (t >= off2 ? 1u : 0u) + (t >= off3 ? 1u : 0u);
+                    const uint32_t tl = t - (w == 0 ? 0u : w == 1 ? off1 : w == 2 ? off2 : off3);
+                    uint32_t p = w * (kVpt * 32);
 #pragma unroll
-                    for (uint32_t step = kChunk / 2; step >= 1; step >>= 1)
-                        if (sh.incl[p + step - 1] <= t) p += step;
+                    for (uint32_t step = kVpt * 16; step >= 1; step >>= 1)
+                        if (sh.incl[p + step - 1] <= tl) p += step;
                     nob = sh.beg[p];
                     noe = sh.end[p];
-                    const uint32_t first = p ? sh.incl[p - 1] : 0u;
-                    nq = (static_cast<uint32_t>(nob) >> 2) + (t - first);
+                    const uint32_t first = (p & (kVpt * 32 - 1)) ? sh.incl[p - 1] : 0u;
+                    nq = (static_cast<uint32_t>(nob) >> 2) + (tl - first);
                     nul = base + p;
                     nth = __ldg(P.g.thr4 + nq);
                 }
