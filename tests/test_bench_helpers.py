@@ -1,0 +1,56 @@
+"""Host logic of bench.py (CPU): the algorithmic-bytes formula of the roofline, the rule that ties
+ncu traffic to the kernel sources it was measured on, and the bench line's argument handling."""
+from __future__ import annotations
+
+import os
+
+import bench
+
+
+def _stats(reached, examined, live, samples):
+    z = [0, 0, 0, 0]
+    st = {"tier_reached": list(z), "tier_examined_edges": list(z), "tier_live_edges": list(z),
+          "tier_samples": list(z)}
+    st["tier_reached"][3], st["tier_examined_edges"][3] = reached, examined
+    st["tier_live_edges"][3], st["tier_samples"][3] = live, samples
+    return st
+
+
+def test_algorithmic_bytes_formula():
+    # 10 samples, 3 seeds each: 8|R| + 4 E_R + 4 L + 8 |R \ S|
+    st = _stats(reached=500, examined=7000, live=420, samples=10)
+    assert bench.algorithmic_bytes(st, 3, 3) == 8 * 500 + 4 * 7000 + 4 * 420 + 8 * (500 - 30)
+    assert bench.algorithmic_bytes(_stats(0, 0, 0, 0), 3, 50) == 0
+
+
+def test_traffic_only_for_the_sources_it_was_measured_on(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    csrc = tmp_path / "paper_2302_13529_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES:
+        (csrc / f).write_text(f"// {f} v1\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.kernel_source_hash()
+    path = prof / f"k_sample_cta_{bench.WORKLOAD}.md"
+    path.write_text(f"# x\nsource_hash: {h}\ndram_bytes_per_launch: 1234\n")
+    assert bench.ncu_traffic("k_sample_cta") == 1234.0
+    (csrc / bench.KERNEL_SOURCES[0]).write_text("// changed\n")  # the kernel changed since
+    assert bench.kernel_source_hash() != h
+    assert bench.ncu_traffic("k_sample_cta") is None
+    assert bench.ncu_traffic("k_other") is None  # no summary at all
+
+
+def test_committed_profile_names_its_kernel_sources():
+    """The committed block-tier summary carries a source hash and a traffic figure."""
+    path = os.path.join(bench.ROOT, "profiles", f"k_sample_cta_{bench.WORKLOAD}.md")
+    text = open(path).read()
+    assert "source_hash:" in text and "dram_bytes_per_launch:" in text
+
+
+def test_default_arguments_are_the_driver_contract():
+    a = bench.parse_args([])
+    assert (a.gpus, a.workload, a.impl) == (1, "rmat17", "ours")
+    assert a.warmup >= 3 and a.steps >= 1
+    a = bench.parse_args(["--workload", "rmat22", "--b", "2", "--theta", "500"])
+    assert (a.b, a.theta) == (2, 500)
