@@ -253,8 +253,9 @@ int imin_estimate_decrease_stats(const imin_graph* g, const int32_t* seeds, int3
  * calls (round 0 of `key`, no blockers; each sized to take about 2 ms, at most 24 samples per
  * resident block of the block tier and at most 65,536) for each candidate cutoff
  * {0, 64, 96, 128, 192} (0 = block tier only), interleaved, and keeps the candidate with the
- * smallest minimum time. When fewer than 4 samples per block fit in 2 ms (huge cascades), it keeps
- * 96 without timing. The first warm-up call samples at most 1,024 graphs (at most the caller's
+ * smallest minimum time. When fewer than 4 samples per block fit in 2 ms (huge cascades), it does
+ * not time the candidates: it keeps 96 if the warm-up's warp tier finished at least a tenth of
+ * its samples, and 0 otherwise. The first warm-up call samples at most 1,024 graphs (at most the caller's
  * theta for the lazy tuning).
  * The cutoff never changes any result of this library, only which kernel computes a sample.
  * The estimate and greedy calls tune lazily on first use for each graph and seed-set size class

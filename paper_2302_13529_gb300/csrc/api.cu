@@ -443,8 +443,9 @@ int size_class(size_t ns)
 }
 
 // Device time of one Alg. 2 call (round 0, no blockers) with the given cutoff.
+// warp_done (optional): receives the number of samples the warp tier 0 finished.
 int time_call(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t key, uint32_t cutoff,
-              uint32_t theta, cudaStream_t s, float* ms)
+              uint32_t theta, cudaStream_t s, float* ms, unsigned long long* warp_done = nullptr)
 {
     Query q(s);
     int rc = setup_query(g, seeds, theta, nullptr, cutoff, q);
@@ -467,11 +468,14 @@ int time_call(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t k
         T.collect();
     }
     std::vector<RoundCtl> hctl(1);
+    unsigned long long hstats[kStCount] = {};
     if (e == cudaSuccess) e = cudaMemcpyAsync(hctl.data(), ctl, sizeof(RoundCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hstats, q.stats, sizeof(hstats), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     IMIN_CUDA(e);
+    if (warp_done != nullptr) *warp_done = hstats[kStSamples];  // tier 0's slots come first
     return check_ctl(hctl);
 }
 
@@ -483,11 +487,14 @@ int tune_cutoff(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t
     float warm = 0.f, t[kCand];
     const uint32_t blocks = cta_blocks(g, seeds.size());
     const uint32_t tw = std::max<uint32_t>(1, std::min<uint32_t>(1024, theta_hint ? theta_hint : 1024));
-    int rc = time_call(g, seeds, key, kDefaultCutoff, tw, s, &warm);  // warm-up and cost estimate
+    unsigned long long warp_done = 0;
+    int rc = time_call(g, seeds, key, kDefaultCutoff, tw, s, &warm, &warp_done);  // warm-up, cost
     if (rc) return rc;
     double per_sample = std::max(1e-7, static_cast<double>(warm) / tw);  // ms
-    if (kTuneCallMs / per_sample < 4.0 * blocks) {  // too costly to compare: keep the default
-        *out = kDefaultCutoff;
+    if (kTuneCallMs / per_sample < 4.0 * blocks) {
+        // too costly to compare by timing: keep the warp tier only if it finished at least a
+        // tenth of the warm-up's samples (otherwise its partial work is mostly thrown away)
+        *out = 10 * warp_done >= tw ? kDefaultCutoff : 0u;
         return IMIN_OK;
     }
     // a small warm-up is dominated by its slowest block; re-estimate on a call of the planned size
