@@ -46,6 +46,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--ref-step-seconds", type=float, default=10.0,
+                   help="--impl reference: target host time of one step (a bounded sample)")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--workload", choices=("rmat17", "batch256", "serving", "rmat22"), default="rmat17",
@@ -223,7 +225,7 @@ def run_reference(args, q, rank):
     t = time.perf_counter()
     O.decrease(q.graph, q.seeds, [], 100, q.key, 0)
     per = (time.perf_counter() - t) / 100
-    per_step = int(max(100, min(q.theta, 10.0 / max(per, 1e-7))))
+    per_step = int(max(100, min(q.theta, args.ref_step_seconds / max(per, 1e-7))))
     for w in range(args.warmup):
         O.decrease(q.graph, q.seeds, [], min(per_step, 200), q.key, w)
     times = []

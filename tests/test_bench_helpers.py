@@ -54,3 +54,22 @@ def test_default_arguments_are_the_driver_contract():
     assert a.warmup >= 3 and a.steps >= 1
     a = bench.parse_args(["--workload", "rmat22", "--b", "2", "--theta", "500"])
     assert (a.b, a.theta) == (2, 500)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one JSON line with the
+    metric, unit and config of the GPU arm, its CPU-baseline description and a zero-copy e2e."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "2", "--warmup", "1", "--ref-step-seconds", "0.2"],
+                         capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "samples/s" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["config"]["workload"] == bench.WORKLOAD
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"] == {"value": line["value"], "unit": "samples/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
