@@ -39,3 +39,34 @@ def test_null_handle_is_rejected_without_gpu_work():
     lib = ctypes.CDLL(build.build())
     assert lib.imin_graph_info(None, None, None) == -1
     assert lib.imin_free_graph(None) == 0
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """The product path has no CPU fallback: with libimin.so missing, the binding raises instead
+    of computing anything."""
+    import pytest
+    from paper_2302_13529_gb300 import imin
+    monkeypatch.setattr(imin, "_lib", None)
+    monkeypatch.setattr(imin, "LIB", str(tmp_path / "missing" / "libimin.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        imin.lib()
+
+
+def test_invalid_calls_are_rejected_on_the_host():
+    """Argument checks that need no GPU work return IMIN_ERR_INVALID with a message."""
+    lib = ctypes.CDLL(build.build())
+    lib.imin_last_error.restype = ctypes.c_char_p
+    out = ctypes.c_void_p()
+    # a malformed CSR: row_ptr does not end at m
+    rp = (ctypes.c_int32 * 3)(0, 1, 5)
+    col = (ctypes.c_int32 * 1)(0)
+    thr = (ctypes.c_uint32 * 1)(1)
+    lib.imin_load_graph.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    rc = lib.imin_load_graph(2, 1, ctypes.cast(rp, ctypes.c_void_p), ctypes.cast(col, ctypes.c_void_p),
+                             ctypes.cast(thr, ctypes.c_void_p), None, ctypes.byref(out))
+    assert rc == -1 and lib.imin_last_error()
+    lib.imin_estimate_decrease.argtypes = [ctypes.c_void_p] * 2 + [ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64,
+                                            ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.imin_estimate_decrease(None, None, 1, None, 0, 1, 0, 0, None, None) == -1
