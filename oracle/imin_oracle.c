@@ -35,6 +35,9 @@
  *     candidates in ascending vertex id (so the smallest id wins ties).
  *   - The expected spread E(S, G[V \ B]) (Def. 3) by simulation: the sum of |R| (seeds
  *     included) over sampled graphs of the same stream.
+ *   - Every entry point also runs under the linear-threshold model, the standard triggering
+ *     model (Sec. 4.5), selected by its last argument (0: IC, 1: LT); only the live-edge
+ *     decision changes (see the LT section below).
  *
  * Philox4x32-10 is written from J. K. Salmon, M. A. Moraes, R. O. Dror, D. E. Shaw,
  * "Parallel Random Numbers: As Easy as 1, 2, 3", SC'11, Sec. 3.3 (Philox): 4 x 32-bit counter,
@@ -106,6 +109,26 @@ static int edge_live(uint64_t key, uint32_t round, uint32_t sample, int64_t e, u
 }
 
 /* ------------------------------------------------------------------------------------------
+ * Linear-threshold model, the best-known triggering model (Sec. 4.5: every vertex v draws a
+ * triggering set from a distribution over subsets of its in-neighbours, and only edges from that
+ * set stay). In the LT model the set holds at most one in-neighbour: edge (u, v) with probability
+ * b(u, v), none with probability 1 - sum_u b(u, v). Encoding: thr[e] + 1 is edge e's share of
+ * 2^32 (the same fixed point as the IC thresholds), the in-edges of v in ascending edge id take
+ * consecutive intervals [lo_e, lo_e + thr[e]] of [0, 2^32), and sample j keeps edge e = (u, v)
+ * iff v's word of that sample lies in e's interval. v's word is one 32-bit word of the same
+ * Philox stream, counter (v >> 2, j, round, 0x80000000), word v & 3 -- the last counter word
+ * keeps vertex words apart from edge words, whose last counter word is e >> 34 < 2^29.
+ * ---------------------------------------------------------------------------------------- */
+ORACLE_API uint32_t oracle_vertex_word(uint64_t key, uint32_t round, uint32_t sample, int32_t v)
+{
+    uint32_t ctr[4] = {(uint32_t)v >> 2, sample, round, 0x80000000u};
+    uint32_t k[2] = {(uint32_t)key, (uint32_t)(key >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, k, out);
+    return out[v & 3];
+}
+
+/* ------------------------------------------------------------------------------------------
  * growable int32 array
  * ---------------------------------------------------------------------------------------- */
 typedef struct {
@@ -153,8 +176,54 @@ typedef struct {
     int64_t m;
     const int32_t *row_ptr;
     const int32_t *col;
-    const uint32_t *thr;
+    const uint32_t *thr;  /* IC: live threshold; LT: interval width - 1 */
+    const uint32_t *lo;   /* LT: start of each edge's interval; NULL for the IC model */
 } graph_t;
+
+/* Whether edge e = (u, v) is live in sample j of call `round` (Def. 4 for IC; the triggering
+ * set draw above for LT). */
+static int live(const graph_t *g, uint64_t key, uint32_t round, uint32_t sample, int64_t e, int32_t v)
+{
+    if (!g->lo) return edge_live(key, round, sample, e, g->thr[e]);
+    return oracle_vertex_word(key, round, sample, v) - g->lo[e] <= g->thr[e];
+}
+
+/* LT: lo[e] for every edge; fails when the shares of some vertex's in-edges exceed 2^32. */
+static int lt_offsets(const graph_t *g, uint32_t *lo)
+{
+    uint64_t *acc = (uint64_t *)calloc((size_t)g->n + 1, sizeof(uint64_t));
+    if (!acc) return -1;
+    int rc = 0;
+    for (int64_t e = 0; e < g->m && !rc; e++) {
+        int32_t v = g->col[e];
+        if (v < 0 || v >= g->n) {
+            rc = -1;
+            break;
+        }
+        lo[e] = (uint32_t)acc[v];
+        acc[v] += (uint64_t)g->thr[e] + 1;
+        if (acc[v] > (1ull << 32)) rc = -1;
+    }
+    free(acc);
+    return rc;
+}
+
+/* model 0: IC (Def. 4); model 1: LT. For LT, *lo receives the interval starts (free it). */
+static int graph_model(graph_t *g, int32_t model, uint32_t **lo)
+{
+    *lo = NULL;
+    g->lo = NULL;
+    if (model == 0) return 0;
+    if (model != 1) return -1;
+    *lo = (uint32_t *)malloc(((size_t)g->m + 1) * sizeof(uint32_t));
+    if (!*lo || lt_offsets(g, *lo)) {
+        free(*lo);
+        *lo = NULL;
+        return -1;
+    }
+    g->lo = *lo;
+    return 0;
+}
 
 typedef struct {
     /* size n */
@@ -380,7 +449,7 @@ static int run_sample(const graph_t *g, const int32_t *seeds, int32_t ns, uint64
         for (int64_t e = g->row_ptr[u]; e < g->row_ptr[u + 1]; e++) {
             int32_t v = g->col[e];
             if (s->is_seed[v] || s->is_blocked[v]) continue;
-            if (!edge_live(key, round, sample, e, g->thr[e])) continue;
+            if (!live(g, key, round, sample, e, v)) continue;
             if (s->local[v] == 0) {
                 s->local[v] = (int32_t)s->gid.n;
                 if (iv_push(&s->gid, v)) return -1;
@@ -419,11 +488,16 @@ ORACLE_API int oracle_sample(int32_t n, int64_t m, const int32_t *row_ptr, const
                              const uint32_t *thr, const int32_t *seeds, int32_t ns,
                              const int32_t *blocked, int32_t nb, uint64_t key, uint32_t round,
                              uint32_t sample, uint32_t *c_out, int32_t *idom_out,
-                             int64_t *n_reached, int64_t *n_live)
+                             int64_t *n_reached, int64_t *n_live, int32_t model)
 {
-    graph_t g = {n, m, row_ptr, col, thr};
+    graph_t g = {n, m, row_ptr, col, thr, NULL};
+    uint32_t *lo = NULL;
+    if (graph_model(&g, model, &lo)) return -1;
     state_t s;
-    if (state_init(&s, n)) return -1;
+    if (state_init(&s, n)) {
+        free(lo);
+        return -1;
+    }
     int rc = validate(&g, seeds, ns, blocked, nb, &s);
     if (!rc) rc = run_sample(&g, seeds, ns, key, round, sample, &s);
     if (!rc) {
@@ -440,6 +514,7 @@ ORACLE_API int oracle_sample(int32_t n, int64_t m, const int32_t *row_ptr, const
         *n_live = s.esrc.n - ns;
     }
     state_free(&s);
+    free(lo);
     return rc;
 }
 
@@ -466,17 +541,23 @@ ORACLE_API int oracle_decrease_range(int32_t n, int64_t m, const int32_t *row_pt
                                      const int32_t *col, const uint32_t *thr,
                                      const int32_t *seeds, int32_t ns, const int32_t *blocked,
                                      int32_t nb, uint64_t key, uint32_t round, uint32_t j0,
-                                     uint32_t j1, uint64_t *delta)
+                                     uint32_t j1, uint64_t *delta, int32_t model)
 {
-    graph_t g = {n, m, row_ptr, col, thr};
+    graph_t g = {n, m, row_ptr, col, thr, NULL};
+    uint32_t *lo = NULL;
+    if (graph_model(&g, model, &lo)) return -1;
     state_t s;
-    if (state_init(&s, n)) return -1;
+    if (state_init(&s, n)) {
+        free(lo);
+        return -1;
+    }
     int rc = validate(&g, seeds, ns, blocked, nb, &s);
     if (!rc) {
         memset(delta, 0, (size_t)n * sizeof(uint64_t));
         rc = decrease_range(&g, seeds, ns, key, round, j0, j1, delta, &s);
     }
     state_free(&s);
+    free(lo);
     return rc;
 }
 
@@ -484,10 +565,10 @@ ORACLE_API int oracle_decrease_range(int32_t n, int64_t m, const int32_t *row_pt
 ORACLE_API int oracle_decrease(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
                                const uint32_t *thr, const int32_t *seeds, int32_t ns,
                                const int32_t *blocked, int32_t nb, uint32_t theta, uint64_t key,
-                               uint32_t round, uint64_t *delta)
+                               uint32_t round, uint64_t *delta, int32_t model)
 {
     return oracle_decrease_range(n, m, row_ptr, col, thr, seeds, ns, blocked, nb, key, round, 0,
-                                 theta, delta);
+                                 theta, delta, model);
 }
 
 /* ------------------------------------------------------------------------------------------
@@ -513,7 +594,7 @@ static int reach_count(const graph_t *g, const int32_t *seeds, int32_t ns, uint6
         for (int64_t e = g->row_ptr[u]; e < g->row_ptr[u + 1]; e++) {
             int32_t v = g->col[e];
             if (s->local[v] != 0 || s->is_blocked[v]) continue;
-            if (!edge_live(key, round, sample, e, g->thr[e])) continue;
+            if (!live(g, key, round, sample, e, v)) continue;
             s->local[v] = (int32_t)s->gid.n;
             if (iv_push(&s->gid, v)) return -1;
         }
@@ -526,11 +607,16 @@ static int reach_count(const graph_t *g, const int32_t *seeds, int32_t ns, uint6
 ORACLE_API int oracle_spread_range(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
                                    const uint32_t *thr, const int32_t *seeds, int32_t ns,
                                    const int32_t *blocked, int32_t nb, uint64_t key, uint32_t round,
-                                   uint32_t j0, uint32_t j1, uint64_t *out_sum)
+                                   uint32_t j0, uint32_t j1, uint64_t *out_sum, int32_t model)
 {
-    graph_t g = {n, m, row_ptr, col, thr};
+    graph_t g = {n, m, row_ptr, col, thr, NULL};
+    uint32_t *lo = NULL;
+    if (graph_model(&g, model, &lo)) return -1;
     state_t s;
-    if (state_init(&s, n)) return -1;
+    if (state_init(&s, n)) {
+        free(lo);
+        return -1;
+    }
     int rc = validate(&g, seeds, ns, blocked, nb, &s);
     uint64_t total = 0;
     for (uint32_t j = j0; !rc && j < j1; j++) {
@@ -541,6 +627,7 @@ ORACLE_API int oracle_spread_range(int32_t n, int64_t m, const int32_t *row_ptr,
     }
     if (!rc) *out_sum = total;
     state_free(&s);
+    free(lo);
     return rc;
 }
 
@@ -559,12 +646,20 @@ ORACLE_API int oracle_advanced_greedy(int32_t n, int64_t m, const int32_t *row_p
                                       const int32_t *col, const uint32_t *thr,
                                       const int32_t *seeds, int32_t ns, int32_t b,
                                       uint32_t theta, uint64_t key, int32_t *out_blockers,
-                                      int32_t *out_count)
+                                      int32_t *out_count, int32_t model)
 {
-    graph_t g = {n, m, row_ptr, col, thr};
+    graph_t g = {n, m, row_ptr, col, thr, NULL};
+    uint32_t *lo = NULL;
+    if (graph_model(&g, model, &lo)) return -1;
     state_t s;
-    if (b < 0 || theta == 0) return -1;
-    if (state_init(&s, n)) return -1;
+    if (b < 0 || theta == 0) {
+        free(lo);
+        return -1;
+    }
+    if (state_init(&s, n)) {
+        free(lo);
+        return -1;
+    }
     int rc = validate(&g, seeds, ns, NULL, 0, &s);
     uint64_t *delta = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
     uint8_t *cand = (uint8_t *)calloc((size_t)n + 1, 1);
@@ -590,6 +685,7 @@ ORACLE_API int oracle_advanced_greedy(int32_t n, int64_t m, const int32_t *row_p
     free(delta);
     free(cand);
     state_free(&s);
+    free(lo);
     return rc;
 }
 
@@ -604,12 +700,20 @@ ORACLE_API int oracle_greedy_replace(int32_t n, int64_t m, const int32_t *row_pt
                                      const int32_t *col, const uint32_t *thr,
                                      const int32_t *seeds, int32_t ns, int32_t b,
                                      uint32_t theta, uint64_t key, int32_t *out_blockers,
-                                     int32_t *out_count)
+                                     int32_t *out_count, int32_t model)
 {
-    graph_t g = {n, m, row_ptr, col, thr};
+    graph_t g = {n, m, row_ptr, col, thr, NULL};
+    uint32_t *lo = NULL;
+    if (graph_model(&g, model, &lo)) return -1;
     state_t s;
-    if (b < 0 || theta == 0) return -1;
-    if (state_init(&s, n)) return -1;
+    if (b < 0 || theta == 0) {
+        free(lo);
+        return -1;
+    }
+    if (state_init(&s, n)) {
+        free(lo);
+        return -1;
+    }
     int rc = validate(&g, seeds, ns, NULL, 0, &s);
     uint64_t *delta = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
     uint8_t *cand = (uint8_t *)calloc((size_t)n + 1, 1);
@@ -655,5 +759,6 @@ ORACLE_API int oracle_greedy_replace(int32_t n, int64_t m, const int32_t *row_pt
     free(delta);
     free(cand);
     state_free(&s);
+    free(lo);
     return rc;
 }

@@ -2,7 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY: the oracle states what the sampled-dominator-tree estimator
 (Alg. 2), the greedy drivers AdvancedGreedy (Alg. 3) and GreedyReplace (Alg. 4), and the
-simulated expected spread (Def. 3) compute, slowly and plainly, on the CPU. Only the tests, the smoke check and the benchmark's CPU
+simulated expected spread (Def. 3) compute, slowly and plainly, on the CPU, under the
+independent-cascade model (Def. 4) and under the linear-threshold model, the standard triggering
+model of Sec. 4.5 (model="lt"). Only the tests, the smoke check and the benchmark's CPU
 baseline use it; the product path never imports it.
 
 All functions take numpy arrays; graphs are (n, row_ptr int32[n+1], col int32[m],
@@ -70,11 +72,25 @@ def lib():
             L.oracle_spread_range.argtypes = g + [_i32p, ctypes.c_int32, _i32p, ctypes.c_int32,
                                                   ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                                   ctypes.c_uint32, _u64p]
+            L.oracle_vertex_word.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.c_int32]
+            L.oracle_vertex_word.restype = ctypes.c_uint32
             for name in ("oracle_sample", "oracle_decrease_range", "oracle_decrease",
                          "oracle_advanced_greedy", "oracle_greedy_replace", "oracle_spread_range"):
-                getattr(L, name).restype = ctypes.c_int
+                f = getattr(L, name)
+                f.argtypes = f.argtypes + [ctypes.c_int32]  # model: 0 = IC, 1 = LT
+                f.restype = ctypes.c_int
             _lib = L
     return _lib
+
+
+MODELS = {"ic": 0, "lt": 1}
+
+
+def _model(model: str) -> int:
+    if model not in MODELS:
+        raise ValueError(f"unknown model {model!r} (ic or lt)")
+    return MODELS[model]
 
 
 def _g(n, row_ptr, col, thr):
@@ -107,8 +123,15 @@ def edge_word(key: int, round_: int, sample: int, e: int) -> int:
     return int(lib().oracle_edge_word(key, round_, sample, e))
 
 
-def sample(graph, seeds, blocked, key, round_, j):
-    """One sampled graph: returns (c[n] subtree sizes, idom[n] global ids or -1, |R|, #live)."""
+def vertex_word(key: int, round_: int, sample: int, v: int) -> int:
+    """The uint32 word that decides vertex v's triggering draw in sample `sample` of call
+    `round_` (LT model)."""
+    return int(lib().oracle_vertex_word(key, round_, sample, v))
+
+
+def sample(graph, seeds, blocked, key, round_, j, model="ic"):
+    """One sampled graph: returns (c[n] subtree sizes, idom[n] global ids or -1, |R|, #live).
+    model: "ic" (Def. 4, thr = live threshold) or "lt" (thr + 1 = the edge's share of 2^32)."""
     n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
     s, ns = _ids(seeds)
     b, nb = _ids(blocked)
@@ -117,11 +140,11 @@ def sample(graph, seeds, blocked, key, round_, j):
     nr = ctypes.c_int64()
     nl = ctypes.c_int64()
     _check(lib().oracle_sample(n, m, rp, col, thr, s, ns, b, nb, key, round_, j, c, idom,
-                               ctypes.byref(nr), ctypes.byref(nl)), "sample")
+                               ctypes.byref(nr), ctypes.byref(nl), _model(model)), "sample")
     return c[:n], idom[:n], nr.value, nl.value
 
 
-def decrease(graph, seeds, blocked, theta, key, round_=0, j0=0) -> np.ndarray:
+def decrease(graph, seeds, blocked, theta, key, round_=0, j0=0, model="ic") -> np.ndarray:
     """Alg. 2 on G[V \\ B]: uint64 Delta[n] = sum of dominator-subtree sizes over samples
     j0 .. j0+theta-1 (no division by theta)."""
     n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
@@ -129,11 +152,11 @@ def decrease(graph, seeds, blocked, theta, key, round_=0, j0=0) -> np.ndarray:
     b, nb = _ids(blocked)
     out = np.zeros(max(n, 1), dtype=np.uint64)
     _check(lib().oracle_decrease_range(n, m, rp, col, thr, s, ns, b, nb, key, round_, j0,
-                                       j0 + theta, out), "decrease")
+                                       j0 + theta, out, _model(model)), "decrease")
     return out[:n]
 
 
-def spread(graph, seeds, blocked, theta, key, round_=0, j0=0) -> int:
+def spread(graph, seeds, blocked, theta, key, round_=0, j0=0, model="ic") -> int:
     """Def. 3 by simulation: the sum of |R| (seeds included) over samples j0 .. j0+theta-1 of
     call `round_` on G[V \\ B]; the expected-spread estimate is this sum / theta."""
     n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
@@ -141,27 +164,27 @@ def spread(graph, seeds, blocked, theta, key, round_=0, j0=0) -> int:
     b, nb = _ids(blocked)
     out = np.zeros(1, dtype=np.uint64)
     _check(lib().oracle_spread_range(n, m, rp, col, thr, s, ns, b, nb, key, round_, j0,
-                                     j0 + theta, out), "spread")
+                                     j0 + theta, out, _model(model)), "spread")
     return int(out[0])
 
 
-def advanced_greedy(graph, seeds, b, theta, key) -> np.ndarray:
+def advanced_greedy(graph, seeds, b, theta, key, model="ic") -> np.ndarray:
     """Alg. 3: blockers in selection order."""
     n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
     s, ns = _ids(seeds)
     out = np.zeros(max(b, 1), dtype=np.int32)
     cnt = ctypes.c_int32()
     _check(lib().oracle_advanced_greedy(n, m, rp, col, thr, s, ns, b, theta, key, out,
-                                        ctypes.byref(cnt)), "advanced_greedy")
+                                        ctypes.byref(cnt), _model(model)), "advanced_greedy")
     return out[:cnt.value].copy()
 
 
-def greedy_replace(graph, seeds, b, theta, key) -> np.ndarray:
+def greedy_replace(graph, seeds, b, theta, key, model="ic") -> np.ndarray:
     """Alg. 4: blockers in list order (a replacement keeps its predecessor's position)."""
     n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
     s, ns = _ids(seeds)
     out = np.zeros(max(b, 1), dtype=np.int32)
     cnt = ctypes.c_int32()
     _check(lib().oracle_greedy_replace(n, m, rp, col, thr, s, ns, b, theta, key, out,
-                                       ctypes.byref(cnt)), "greedy_replace")
+                                       ctypes.byref(cnt), _model(model)), "greedy_replace")
     return out[:cnt.value].copy()

@@ -80,6 +80,16 @@ def wc_thresholds(col: np.ndarray, n: int) -> np.ndarray:
     return ((np.uint64(TWO32 - 1)) // d).astype(np.uint32)
 
 
+def lt_wc_weights(col: np.ndarray, n: int) -> np.ndarray:
+    """Linear-threshold weights b(u,v) = 1/d_in(v), as the shares the LT model takes: edge e into
+    v gets floor(2^32/d) of [0, 2^32) (stored as share - 1, the same fixed point as the IC
+    thresholds), so that the shares of v's in-edges never exceed 2^32 and each edge keeps
+    probability floor(2^32/d)/2^32 <= 1/d."""
+    d_in = np.bincount(col, minlength=n).astype(np.uint64)
+    d = d_in[col]
+    return (np.uint64(TWO32) // d - np.uint64(1)).astype(np.uint32)
+
+
 TR_PROBS = (Fraction(1, 10), Fraction(1, 100), Fraction(1, 1000))
 TR_THRESHOLDS = np.array([threshold_of(p) for p in TR_PROBS], dtype=np.uint32)
 

@@ -110,6 +110,75 @@ def exact_spread_moments(g: Graph, seeds, blocked=(), max_uncertain=18):
     return float(m1), float(m2)
 
 
+def lt_intervals(g: Graph):
+    """LT model: the interval [lo, lo + thr] of [0, 2^32) that each edge takes within its
+    target's share, in ascending edge id per target."""
+    acc = [0] * g.n
+    out = {}
+    for (e, u, v, t) in edges_of(g):
+        out[e] = (acc[v], acc[v] + t)
+        acc[v] += t + 1
+    assert all(a <= TWO32 for a in acc), "in-edge shares exceed 1"
+    return out
+
+
+def lt_sample_live_edges(g: Graph, key, round_, j, vertex_word):
+    """Live edges of LT sample j: edge (u, v) stays iff v's word lies in the edge's interval,
+    so every vertex keeps at most one in-edge (its triggering set)."""
+    iv = lt_intervals(g)
+    words = {}
+    live = []
+    for (e, u, v, t) in edges_of(g):
+        if v not in words:
+            words[v] = vertex_word(key, round_, j, v)
+        lo, hi = iv[e]
+        if lo <= words[v] <= hi:
+            live.append((u, v))
+    return live
+
+
+def exact_lt_moments(g: Graph, seeds, blocked=(), max_worlds=1 << 16):
+    """Exact expectations over all LT triggering draws (each vertex picks one in-edge with
+    probability share/2^32, or none), in exact rationals: (spread, dec[], dec2[]) as in
+    exact_moments."""
+    seeds = list(seeds)
+    blocked = set(blocked)
+    choices = {}
+    for (e, u, v, t) in edges_of(g):
+        choices.setdefault(v, []).append((u, Fraction(t + 1, TWO32)))
+    per_vertex = []
+    for v, opts in choices.items():
+        rest = 1 - sum(p for _, p in opts)
+        per_vertex.append([(u, v, p) for u, p in opts] + ([(None, v, rest)] if rest > 0 else []))
+    worlds = 1
+    for opts in per_vertex:
+        worlds *= len(opts)
+    if worlds > max_worlds:
+        raise ValueError("too many triggering worlds to enumerate")
+    n = g.n
+    spread = Fraction(0)
+    dec = [Fraction(0)] * n
+    dec2 = [Fraction(0)] * n
+    for pick in itertools.product(*per_vertex):
+        pw = Fraction(1)
+        live = []
+        for (u, v, p) in pick:
+            pw *= p
+            if u is not None:
+                live.append((u, v))
+        if pw == 0:
+            continue
+        R = reach(n, live, seeds, blocked)
+        spread += pw * len(R)
+        for u in R:
+            if u in seeds:
+                continue
+            d = len(R) - len(reach(n, live, seeds, blocked | {u}))
+            dec[u] += pw * d
+            dec2[u] += pw * d * d
+    return float(spread), np.array([float(x) for x in dec]), np.array([float(x) for x in dec2])
+
+
 def sample_live_edges(g: Graph, key, round_, j, word):
     """Live edges of sample j: edge e is live iff word(key, round, j, e) <= thr[e] (Def. 4)."""
     return [(u, v) for (e, u, v, t) in edges_of(g) if word(key, round_, j, e) <= t]
