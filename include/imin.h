@@ -125,23 +125,27 @@ int imin_greedy_replace(const imin_graph* g, const int32_t* seeds, int32_t n_see
 
 /* imin_estimate_decrease for callers that cannot allocate memory at call time (the paper has
  * no counterpart; this is a deployment variant).
- * Some callers must not allocate device memory when they call in: code that runs while a stream
- * is being captured into a CUDA graph (cudaMalloc is not allowed during capture), code whose
- * device memory belongs to another allocator with a fixed budget, and latency-critical paths
- * that cannot afford cudaMalloc/cudaFree, which may synchronize the whole device. This entry
- * point computes exactly what imin_estimate_decrease computes (same arguments, same results)
- * but calls no cudaMalloc, cudaFree or other allocating routine: besides the caller's inputs
- * and output, all working memory comes from one static device array of 64 MiB inside the
- * library, which every GPU that loads the library holds until the process exits.
+ * Some callers must not allocate device memory when they call in: code whose device memory
+ * belongs to another allocator with a fixed budget (a framework's caching allocator, a serving
+ * process that sizes all of its memory at start-up), and latency-critical paths that cannot
+ * afford cudaMalloc/cudaFree, which may synchronize the whole device. This entry point computes
+ * exactly what imin_estimate_decrease computes (same arguments, same results) but calls no
+ * cudaMalloc, cudaFree or other allocating routine: besides the caller's inputs and output, all
+ * working memory comes from one static device array of 64 MiB inside the library, which every
+ * GPU that loads the library holds until the process exits.
  * Limits (from that size): n <= 65,536 vertices and theta <= 131,072 samples per call; larger
  * requests fail with IMIN_ERR_INVALID. A sampled cascade that would need the library's
  * whole-graph fallback kernel (more non-tree live edges or BFS levels than the block-per-sample
- * kernel holds) fails the call with IMIN_ERR_CAPACITY.
+ * kernel holds) fails the call with IMIN_ERR_CAPACITY. After any non-OK return the contents of
+ * out_delta are undefined (a device out_delta may hold partial counters).
+ * out_delta may be host memory or device memory of the graph's device (device memory of another
+ * GPU is rejected with IMIN_ERR_INVALID).
  * The static array is shared by all calls on a device and keeps the last call's contents (each
  * call clears what must start at zero); calls that overlap on the GPU race on it, so order them
- * (one stream, or events). The first call on each device performs set-up (it resolves the
- * array's device address and configures the kernel); make that first call before any stream
- * capture. Synchronizes `stream`. */
+ * (one stream, or events). The first call on each device resolves the array's device address,
+ * and the first call for each graph size plans the kernel launch.
+ * The call is synchronous: it synchronizes `stream` before its kernel (to check the seed and
+ * blocked ids) and after it (to read the kernel's status). */
 int imin_estimate_decrease_noalloc(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
                                    const int32_t* blocked, int32_t n_blocked, uint32_t theta,
                                    uint64_t key, uint32_t round, uint64_t* out_delta,

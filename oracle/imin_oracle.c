@@ -55,6 +55,7 @@
  * uses round i-1 in its i-th iteration; GreedyReplace numbers its phase-1 calls first and
  * continues the count through phase 2.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -537,6 +538,134 @@ static int decrease_range(const graph_t *g, const int32_t *seeds, int32_t ns, ui
     return 0;
 }
 
+/* ------------------------------------------------------------------------------------------
+ * Optional parallelism over samples. Alg. 2's counters and the simulated spread are sums over
+ * independent samples, so splitting [j0, j1) into blocks handled by worker threads, each with
+ * its own state and its own partial sums, and adding the partial sums gives exactly the result
+ * of the sequential loop (integer addition is associative). The default is one thread: the
+ * plain sequential loop.
+ * ---------------------------------------------------------------------------------------- */
+static int g_threads = 1;
+
+ORACLE_API void oracle_set_threads(int32_t threads) { g_threads = threads < 1 ? 1 : threads; }
+ORACLE_API int32_t oracle_get_threads(void) { return g_threads; }
+
+enum { SAMPLE_BLOCK = 16 };
+
+typedef struct {
+    const graph_t *g;
+    const int32_t *seeds;
+    int32_t ns;
+    uint64_t key;
+    uint32_t round, j1;
+    const state_t *parent;     /* seed / blocked marks to copy */
+    int spread;                /* 0: Alg. 2 counters; 1: sum of |R| */
+    uint32_t *next;            /* next unclaimed sample (shared) */
+    pthread_mutex_t *mu;
+    uint64_t *delta;           /* this worker's partial counters [n] (Alg. 2) */
+    uint64_t sum;              /* this worker's partial sum of |R| (spread) */
+    int rc;
+} worker_t;
+
+static int reach_count(const graph_t *g, const int32_t *seeds, int32_t ns, uint64_t key,
+                       uint32_t round, uint32_t sample, state_t *s, int64_t *count);
+
+static void *worker_main(void *arg)
+{
+    worker_t *w = (worker_t *)arg;
+    const int32_t n = w->g->n;
+    state_t s;
+    if (state_init(&s, n)) {
+        w->rc = -1;
+        return NULL;
+    }
+    memcpy(s.is_seed, w->parent->is_seed, (size_t)n);
+    memcpy(s.is_blocked, w->parent->is_blocked, (size_t)n);
+    for (;;) {
+        pthread_mutex_lock(w->mu);
+        const uint32_t a = *w->next;
+        const uint32_t b = (w->j1 - a > SAMPLE_BLOCK) ? a + SAMPLE_BLOCK : w->j1;
+        *w->next = b;
+        pthread_mutex_unlock(w->mu);
+        if (a >= w->j1 || w->rc) break;
+        if (!w->spread) {
+            w->rc = decrease_range(w->g, w->seeds, w->ns, w->key, w->round, a, b, w->delta, &s);
+        } else {
+            for (uint32_t j = a; j < b && !w->rc; j++) {
+                int64_t c = 0;
+                w->rc = reach_count(w->g, w->seeds, w->ns, w->key, w->round, j, &s, &c);
+                w->sum += (uint64_t)c;
+                clear_sample(&s);
+            }
+        }
+    }
+    state_free(&s);
+    return NULL;
+}
+
+/* Samples [j0, j1) on g_threads threads: adds Alg. 2's counters into delta (spread = 0) or the
+ * sum of |R| into *sum (spread = 1). s holds the query's seed / blocked marks. */
+static int run_parallel(const graph_t *g, const int32_t *seeds, int32_t ns, uint64_t key,
+                        uint32_t round, uint32_t j0, uint32_t j1, const state_t *s, int spread,
+                        uint64_t *delta, uint64_t *sum)
+{
+    int T = g_threads;
+    if ((int64_t)(j1 - j0) < (int64_t)T * SAMPLE_BLOCK) T = (int)((j1 - j0) / SAMPLE_BLOCK) + 1;
+    worker_t *w = (worker_t *)calloc((size_t)T, sizeof(worker_t));
+    pthread_t *th = (pthread_t *)calloc((size_t)T, sizeof(pthread_t));
+    uint8_t *started = (uint8_t *)calloc((size_t)T, 1);
+    if (!w || !th || !started) {
+        free(w);
+        free(th);
+        free(started);
+        return -1;
+    }
+    pthread_mutex_t mu = PTHREAD_MUTEX_INITIALIZER;
+    uint32_t next = j0;
+    int rc = 0;
+    for (int t = 0; t < T; t++) {
+        w[t] = (worker_t){g, seeds, ns, key, round, j1, s, spread, &next, &mu, NULL, 0, 0};
+        if (!spread) {
+            w[t].delta = (uint64_t *)calloc((size_t)g->n + 1, sizeof(uint64_t));
+            if (!w[t].delta) rc = -1;
+        }
+    }
+    for (int t = 0; t < T && !rc; t++) {
+        if (pthread_create(&th[t], NULL, worker_main, &w[t]) != 0) rc = -1;
+        else started[t] = 1;
+    }
+    if (rc) {  /* stop the workers that started: claim every remaining sample */
+        pthread_mutex_lock(&mu);
+        next = j1;
+        pthread_mutex_unlock(&mu);
+    }
+    for (int t = 0; t < T; t++) {
+        if (started[t]) pthread_join(th[t], NULL);
+        if (!rc && w[t].rc) rc = w[t].rc;
+    }
+    for (int t = 0; t < T; t++) {
+        if (!rc) {
+            if (spread) *sum += w[t].sum;
+            else
+                for (int32_t v = 0; v < g->n; v++) delta[v] += w[t].delta[v];
+        }
+        free(w[t].delta);
+    }
+    free(w);
+    free(th);
+    free(started);
+    return rc;
+}
+
+/* Alg. 2 over samples [j0, j1), adding into delta: the sequential loop, or run_parallel. */
+static int alg2(const graph_t *g, const int32_t *seeds, int32_t ns, uint64_t key, uint32_t round,
+                uint32_t j0, uint32_t j1, uint64_t *delta, state_t *s)
+{
+    if (g_threads <= 1 || j1 - j0 < 2 * SAMPLE_BLOCK)
+        return decrease_range(g, seeds, ns, key, round, j0, j1, delta, s);
+    return run_parallel(g, seeds, ns, key, round, j0, j1, s, 0, delta, NULL);
+}
+
 ORACLE_API int oracle_decrease_range(int32_t n, int64_t m, const int32_t *row_ptr,
                                      const int32_t *col, const uint32_t *thr,
                                      const int32_t *seeds, int32_t ns, const int32_t *blocked,
@@ -554,7 +683,7 @@ ORACLE_API int oracle_decrease_range(int32_t n, int64_t m, const int32_t *row_pt
     int rc = validate(&g, seeds, ns, blocked, nb, &s);
     if (!rc) {
         memset(delta, 0, (size_t)n * sizeof(uint64_t));
-        rc = decrease_range(&g, seeds, ns, key, round, j0, j1, delta, &s);
+        rc = alg2(&g, seeds, ns, key, round, j0, j1, delta, &s);
     }
     state_free(&s);
     free(lo);
@@ -619,17 +748,28 @@ ORACLE_API int oracle_spread_range(int32_t n, int64_t m, const int32_t *row_ptr,
     }
     int rc = validate(&g, seeds, ns, blocked, nb, &s);
     uint64_t total = 0;
-    for (uint32_t j = j0; !rc && j < j1; j++) {
-        int64_t c = 0;
-        rc = reach_count(&g, seeds, ns, key, round, j, &s, &c);
-        total += (uint64_t)c;
-        clear_sample(&s);
+    if (!rc && g_threads > 1 && j1 - j0 >= 2 * SAMPLE_BLOCK) {
+        rc = run_parallel(&g, seeds, ns, key, round, j0, j1, &s, 1, NULL, &total);
+    } else {
+        for (uint32_t j = j0; !rc && j < j1; j++) {
+            int64_t c = 0;
+            rc = reach_count(&g, seeds, ns, key, round, j, &s, &c);
+            total += (uint64_t)c;
+            clear_sample(&s);
+        }
     }
     if (!rc) *out_sum = total;
     state_free(&s);
     free(lo);
     return rc;
 }
+
+/* Number of Alg. 2 calls the last AdvancedGreedy / GreedyReplace call of this process made
+ * (GreedyReplace: its phase-1 calls plus the phase-2 calls up to and including the one that
+ * stopped the walk). */
+static int32_t g_last_calls = 0;
+
+ORACLE_API int32_t oracle_last_calls(void) { return g_last_calls; }
 
 /* strict-'>' argmax over candidate vertices in ascending id; -1 if there is none */
 static int32_t argmax_mask(const uint64_t *delta, int32_t n, const uint8_t *is_cand)
@@ -665,6 +805,7 @@ ORACLE_API int oracle_advanced_greedy(int32_t n, int64_t m, const int32_t *row_p
     uint8_t *cand = (uint8_t *)calloc((size_t)n + 1, 1);
     if (!delta || !cand) rc = -1;
     int32_t count = 0;
+    g_last_calls = 0;
     if (!rc) {
         int32_t left = 0;
         for (int32_t u = 0; u < n; u++) {
@@ -673,7 +814,8 @@ ORACLE_API int oracle_advanced_greedy(int32_t n, int64_t m, const int32_t *row_p
         }
         for (int32_t i = 0; i < b && left > 0; i++, left--) {
             memset(delta, 0, (size_t)n * sizeof(uint64_t));
-            rc = decrease_range(&g, seeds, ns, key, (uint32_t)i, 0, theta, delta, &s);
+            rc = alg2(&g, seeds, ns, key, (uint32_t)i, 0, theta, delta, &s);
+            g_last_calls = i + 1;
             if (rc) break;
             int32_t x = argmax_mask(delta, n, cand);
             out_blockers[count++] = x;
@@ -720,6 +862,7 @@ ORACLE_API int oracle_greedy_replace(int32_t n, int64_t m, const int32_t *row_pt
     if (!delta || !cand) rc = -1;
     int32_t count = 0;
     uint32_t round = 0;
+    g_last_calls = 0;
     if (!rc) {
         /* CB: out-neighbours of the seeds that are not seeds themselves */
         for (int32_t i = 0; i < ns; i++) {
@@ -732,7 +875,7 @@ ORACLE_API int oracle_greedy_replace(int32_t n, int64_t m, const int32_t *row_pt
         int32_t rounds = ncb < b ? ncb : b;
         for (int32_t i = 0; i < rounds && !rc; i++) {
             memset(delta, 0, (size_t)n * sizeof(uint64_t));
-            rc = decrease_range(&g, seeds, ns, key, round++, 0, theta, delta, &s);
+            rc = alg2(&g, seeds, ns, key, round++, 0, theta, delta, &s);
             if (rc) break;
             int32_t x = argmax_mask(delta, n, cand);
             cand[x] = 0;
@@ -746,7 +889,7 @@ ORACLE_API int oracle_greedy_replace(int32_t n, int64_t m, const int32_t *row_pt
             s.is_blocked[u] = 0;
             cand[u] = 1;
             memset(delta, 0, (size_t)n * sizeof(uint64_t));
-            rc = decrease_range(&g, seeds, ns, key, round++, 0, theta, delta, &s);
+            rc = alg2(&g, seeds, ns, key, round++, 0, theta, delta, &s);
             if (rc) break;
             int32_t x = argmax_mask(delta, n, cand);
             out_blockers[i] = x;
@@ -756,6 +899,7 @@ ORACLE_API int oracle_greedy_replace(int32_t n, int64_t m, const int32_t *row_pt
         }
     }
     *out_count = count;
+    if (round > 0) g_last_calls = (int32_t)round;
     free(delta);
     free(cand);
     state_free(&s);

@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra", "-shared", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra", "-pthread", "-shared", "-fPIC",
                                "-o", tmp, _SRC])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -75,6 +75,10 @@ def lib():
             L.oracle_vertex_word.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                              ctypes.c_int32]
             L.oracle_vertex_word.restype = ctypes.c_uint32
+            L.oracle_set_threads.argtypes = [ctypes.c_int32]
+            L.oracle_set_threads.restype = None
+            L.oracle_get_threads.restype = ctypes.c_int32
+            L.oracle_last_calls.restype = ctypes.c_int32
             for name in ("oracle_sample", "oracle_decrease_range", "oracle_decrease",
                          "oracle_advanced_greedy", "oracle_greedy_replace", "oracle_spread_range"):
                 f = getattr(L, name)
@@ -109,6 +113,38 @@ def _ids(a):
 def _check(rc, what):
     if rc != 0:
         raise ValueError(f"oracle {what} rejected its input (rc={rc})")
+
+
+def set_threads(threads: int) -> None:
+    """Worker threads for the sample loops of Alg. 2 and of the spread simulation (default 1,
+    the plain sequential loop). The sums over samples are integers, so every thread count gives
+    exactly the same results."""
+    lib().oracle_set_threads(int(threads))
+
+
+def get_threads() -> int:
+    return int(lib().oracle_get_threads())
+
+
+class threads:
+    """Context manager: run the oracle's sample loops on `count` threads inside the block."""
+
+    def __init__(self, count: int):
+        self.count = int(count)
+
+    def __enter__(self):
+        self.prev = get_threads()
+        set_threads(self.count)
+        return self
+
+    def __exit__(self, *exc):
+        set_threads(self.prev)
+
+
+def last_calls() -> int:
+    """Alg. 2 calls made by the last advanced_greedy / greedy_replace call of this process
+    (GreedyReplace: phase 1 plus the phase-2 calls up to the one that stopped the walk)."""
+    return int(lib().oracle_last_calls())
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

@@ -1,10 +1,12 @@
 // noalloc.cu -- imin_estimate_decrease_noalloc: one Alg. 2 call that allocates no memory.
 //
-// Who needs it: callers that must not allocate device memory at call time -- code that runs
-// while a stream is being captured into a CUDA graph (cudaMalloc is not allowed there), code
-// whose device memory is owned by another allocator with a fixed budget (a framework's caching
-// allocator, a serving process that pre-sizes everything at start-up), and latency-critical
-// paths that cannot afford cudaMalloc/cudaFree, which may synchronize the whole device.
+// Who needs it: callers that must not allocate device memory when they call in -- code whose
+// device memory is owned by another allocator with a fixed budget (a framework's caching
+// allocator, a serving process that sizes everything at start-up and must not grow later), and
+// latency-critical paths that cannot afford cudaMalloc/cudaFree, which may synchronize the whole
+// device. The call itself is synchronous: it reads a validation flag back from the device before
+// its kernel runs and the kernel's status after it, so it returns only when the counters are
+// final, and it cannot be recorded into a CUDA graph by stream capture.
 //
 // What it does: exactly what imin_estimate_decrease computes, with the block-per-sample tier
 // (sample_cta.cu), but every byte of working memory it needs besides the caller's inputs and
@@ -13,7 +15,8 @@
 // graphs with at most kNoAllocMaxVertices vertices and at most kNoAllocMaxTheta samples per call;
 // bigger requests are rejected with IMIN_ERR_INVALID. A sampled cascade that would need the
 // whole-graph fallback tier (more non-tree live edges or BFS levels than the block tier holds)
-// makes the call fail with IMIN_ERR_CAPACITY instead of running that tier.
+// makes the call fail with IMIN_ERR_CAPACITY instead of running that tier; out_delta then holds
+// partial counters and must not be used.
 //
 // The array is shared by every call on a device and keeps the last call's contents; each call
 // clears the parts that must start at zero. Calls that overlap on the GPU (different streams or
@@ -21,8 +24,10 @@
 //
 // Set-up: the first call on each device resolves the array's device address with
 // cudaGetSymbolAddress (in host code the array's name is only a host-side stand-in, never a
-// device address) and configures the kernel's shared-memory limit; make that first call before
-// any stream capture.
+// device address). The block tier's launch plan (slot layout, grid, shared memory) is computed
+// once per device and graph size (n, m) and kept in a fixed table, so later calls of the same
+// size make no attribute or occupancy queries; the plan's test hooks (IMIN_CTA_EDGE_CAP) are read
+// only when a plan is made.
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -43,6 +48,40 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_setup_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
+
+// Launch plans of the block tier, per device and graph size, in a fixed table (no heap use).
+struct PlanEntry {
+    int device;
+    int32_t n, m;
+    CtaCfg cfg;
+    uint32_t blocks;
+    uint64_t smem;
+};
+constexpr int kPlanSlots = 16;
+PlanEntry g_plans[kPlanSlots];
+int g_plan_count = 0, g_plan_next = 0;
+
+// The block tier's plan for (device, n, m), made on first use.
+bool cta_plan(const imin_graph* g, CtaCfg* cfg, uint32_t* blocks, uint64_t* smem)
+{
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    for (int i = 0; i < g_plan_count; ++i) {
+        const PlanEntry& e = g_plans[i];
+        if (e.device == g->device && e.n == g->n && e.m == g->m) {
+            *cfg = e.cfg;
+            *blocks = e.blocks;
+            *smem = e.smem;
+            return true;
+        }
+    }
+    uint64_t slot_total = 0;
+    if (!plan_cta_tier(g->dev, g->n, g->m, cfg, blocks, smem, &slot_total)) return false;
+    PlanEntry& e = g_plans[g_plan_next];
+    e = PlanEntry{g->device, g->n, g->m, *cfg, *blocks, *smem};
+    g_plan_next = (g_plan_next + 1) % kPlanSlots;
+    if (g_plan_count < kPlanSlots) ++g_plan_count;
+    return true;
+}
 
 // Device address of the static array on `device` (resolved once per device).
 int scratch_address(int device, uint8_t** out)
@@ -82,14 +121,16 @@ __global__ void k_mark_ids(const int32_t* ids, int32_t count, int32_t n, uint32_
 
 uint64_t up256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
-bool device_pointer(const void* p)
+// 1: device (or managed) memory of `device`; 0: host memory; -1: device memory of another GPU.
+int device_pointer(const void* p, int device)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return 0;
+    return a.device == device ? 1 : -1;
 }
 
 int cuda_fail(cudaError_t e, const char* what)
@@ -149,7 +190,10 @@ extern "C" int imin_estimate_decrease_noalloc(const imin_graph* g, const int32_t
 
     // layout of the static array for this call
     const uint32_t words = static_cast<uint32_t>((g->n + 31) / 32);
-    const bool dev_out = device_pointer(out_delta);
+    const int where_out = device_pointer(out_delta, g->device);
+    if (where_out < 0)
+        return fail_msg(IMIN_ERR_INVALID, "out_delta is device memory of another GPU than the graph's");
+    const bool dev_out = where_out > 0;
     uint64_t o = 0;
     const uint64_t off_ctl = o;     o = up256(o + sizeof(RoundCtl));
     const uint64_t off_bad = o;     o = up256(o + sizeof(uint32_t));
@@ -162,8 +206,8 @@ extern "C" int imin_estimate_decrease_noalloc(const imin_graph* g, const int32_t
 
     CtaCfg cfg{};
     uint32_t blocks = 0;
-    uint64_t smem = 0, slot_total = 0;
-    if (!plan_cta_tier(g->dev, g->n, g->m, &cfg, &blocks, &smem, &slot_total))
+    uint64_t smem = 0;
+    if (!cta_plan(g, &cfg, &blocks, &smem))
         return fail_msg(IMIN_ERR_INTERNAL, "the block-per-sample kernel cannot be configured");
     if (off_slots + cfg.slot_bytes > kNoAllocBytes)
         return fail_msg(IMIN_ERR_INVALID, "imin_estimate_decrease_noalloc: request exceeds the static scratch");

@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import functools
 import math
 import os
 import subprocess
@@ -246,15 +247,32 @@ def tiny_chung_lu_query() -> Query:
     return Query(g, uniform_seeds(g.n, 10, 2001), 10, 10_000, query_key(3001))
 
 
+@functools.lru_cache(maxsize=None)
+def _rmat17_graph() -> Graph:
+    return graph_rmat_wc(17, 1 << 20, seed=1002, name="rmat17-m2^20-wc")
+
+
+@functools.lru_cache(maxsize=None)
+def _rmat22_graph() -> Graph:
+    return graph_rmat_wc(22, 1 << 26, seed=1004, name="rmat22-m2^26-wc")
+
+
 def rmat17_query(graph: Graph | None = None) -> Query:
-    """R-MAT n=2^17, m=2^20, WC, |S|=50, b=50, theta=10^5 (single mid-scale query)."""
-    g = graph or graph_rmat_wc(17, 1 << 20, seed=1002, name="rmat17-m2^20-wc")
+    """R-MAT n=2^17, m=2^20, WC, |S|=50, b=50, theta=10^5 (single mid-scale query). The graph is
+    generated once per process (its arrays must not be modified)."""
+    g = graph or _rmat17_graph()
     return Query(g, uniform_seeds(g.n, 50, 2002), 50, 100_000, query_key(3002))
 
 
 def batch_queries(count: int = 256, seed: int = 1003) -> list[Query]:
     """256 independent queries on Chung-Lu graphs: n log-uniform in [10^3, 2*10^5], mean degree
-    uniform in [5, 20], TR probabilities, |S| uniform in [5, 100], b=20, theta=2*10^4."""
+    uniform in [5, 20], TR probabilities, |S| uniform in [5, 100], b=20, theta=2*10^4. Generated
+    once per process for each (count, seed); the arrays must not be modified."""
+    return list(_batch_queries(count, seed))
+
+
+@functools.lru_cache(maxsize=4)
+def _batch_queries(count: int, seed: int) -> tuple:
     out = []
     for q in range(count):
         rng = np.random.default_rng(seed * 1000 + q)
@@ -267,13 +285,41 @@ def batch_queries(count: int = 256, seed: int = 1003) -> list[Query]:
         k = int(rng.integers(5, 101))
         out.append(Query(g, uniform_seeds(n, k, int(rng.integers(1 << 31))), 20, 20_000,
                          query_key(int(rng.integers(1 << 31)))))
-    return out
+    return tuple(out)
 
 
 def rmat22_query(graph: Graph | None = None) -> Query:
-    """R-MAT n=2^22, m=2^26, WC, |S|=200, b=200, theta=2*10^5 (large single query)."""
-    g = graph or graph_rmat_wc(22, 1 << 26, seed=1004, name="rmat22-m2^26-wc")
+    """R-MAT n=2^22, m=2^26, WC, |S|=200, b=200, theta=2*10^5 (large single query). The graph is
+    generated once per process (its arrays must not be modified)."""
+    g = graph or _rmat22_graph()
     return Query(g, uniform_seeds(g.n, 200, 2004), 200, 200_000, query_key(3004))
+
+
+@dataclasses.dataclass
+class Request:
+    """One serving request: AdvancedGreedy on graph `gi` (0: the R-MAT 2^17 graph, 1: the R-MAT
+    2^22 graph) with its own seeds, budget, theta and key."""
+    gi: int
+    seeds: np.ndarray
+    b: int
+    theta: int
+    key: int
+
+
+def serving_requests(count: int, seed: int = 5000) -> list[Request]:
+    """Requests of the serving workload: each picks the R-MAT 2^17 or the R-MAT 2^22 graph with
+    probability 1/2, |S| uniform in [10, 500], b uniform in [10, 100], theta uniform in
+    [10^4, 10^5], a seeded 64-bit key."""
+    rng = np.random.default_rng(seed)
+    ns = (1 << 17, 1 << 22)
+    out = []
+    for _ in range(count):
+        gi = int(rng.integers(0, 2))
+        k = int(rng.integers(10, 501))
+        seeds = uniform_seeds(ns[gi], k, int(rng.integers(1 << 30)))
+        out.append(Request(gi, seeds, int(rng.integers(10, 101)), int(rng.integers(10_000, 100_001)),
+                           int(rng.integers(1 << 62))))
+    return out
 
 
 def random_small_graph(n: int, m: int, seed: int, p_choices=None) -> Graph:

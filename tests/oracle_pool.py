@@ -1,43 +1,39 @@
-"""Run the CPU oracle over sample ranges in a spawned process pool (full-size parity checks).
+"""The CPU oracle on all host cores, for full-size parity checks.
 
-The oracle is single-threaded; Alg. 2's counters are integer sums over samples, so splitting
-[0, theta) into ranges and adding the partial counters gives exactly the same result.
+Alg. 2's counters and the simulated spread are integer sums over independent samples, so the
+oracle's thread-parallel sample loop (oracle.set_threads) returns exactly what its sequential
+loop returns; this module only picks the thread count (every core of the host) and runs the
+oracle's own entry points with it.
 """
 from __future__ import annotations
 
-import multiprocessing as mp
 import os
 
-import numpy as np
-
-_G = None
-
-
-def _init(n, row_ptr, col, thr):
-    global _G
-    from paper_2302_13529_gb300.workloads import Graph
-    _G = Graph(n, row_ptr, col, thr)
-
-
-def _work(args):
-    from oracle import oracle as O
-    seeds, blocked, j0, cnt, key, round_ = args
-    return O.decrease(_G, seeds, blocked, cnt, key, round_, j0)
+from oracle import oracle as O
 
 
 def workers() -> int:
-    return max(1, min(32, (os.cpu_count() or 2)))
+    return max(1, os.cpu_count() or 1)
 
 
-def decrease(g, seeds, blocked, theta, key, round_, nproc=None, chunks_per_proc=4):
-    """Alg. 2 counters over samples [0, theta), computed by the oracle in parallel."""
-    nproc = nproc or workers()
-    nchunk = max(1, min(theta, nproc * chunks_per_proc))
-    bounds = np.linspace(0, theta, nchunk + 1).astype(np.int64)
-    tasks = [(np.asarray(seeds, np.int32), np.asarray(blocked if blocked is not None else [], np.int32),
-              int(bounds[i]), int(bounds[i + 1] - bounds[i]), int(key), int(round_))
-             for i in range(nchunk) if bounds[i + 1] > bounds[i]]
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(nproc, initializer=_init, initargs=(g.n, g.row_ptr, g.col, g.thr)) as pool:
-        parts = pool.map(_work, tasks)
-    return np.sum(parts, axis=0, dtype=np.uint64)
+def decrease(g, seeds, blocked, theta, key, round_, nproc=None, j0=0):
+    """Alg. 2 counters over samples [j0, j0 + theta) of call `round_`."""
+    with O.threads(nproc or workers()):
+        return O.decrease(g, seeds, blocked if blocked is not None else [], theta, key, round_, j0)
+
+
+def advanced_greedy(g, seeds, b, theta, key, nproc=None):
+    """Alg. 3, every round on all host cores."""
+    with O.threads(nproc or workers()):
+        return O.advanced_greedy(g, seeds, b, theta, key)
+
+
+def greedy_replace(g, seeds, b, theta, key, nproc=None):
+    """Alg. 4, every round on all host cores."""
+    with O.threads(nproc or workers()):
+        return O.greedy_replace(g, seeds, b, theta, key)
+
+
+def spread(g, seeds, blocked, theta, key, round_=0, nproc=None):
+    with O.threads(nproc or workers()):
+        return O.spread(g, seeds, blocked if blocked is not None else [], theta, key, round_)

@@ -48,8 +48,21 @@ def test_toy_graph_counters(cuda_lib):
         got = cuda_lib.estimate_decrease(gh, [0], [], 50_000, key)
         assert np.array_equal(got, want)
     assert list(cuda_lib.advanced_greedy(gh, [0], 2, 20_000, 3)) == [4, 1]
-    assert sorted(cuda_lib.greedy_replace(gh, [0], 2, 20_000, 3)) == [1, 3]
+    assert list(cuda_lib.greedy_replace(gh, [0], 2, 20_000, 3)) == [1, 3]
     assert list(cuda_lib.greedy_replace(gh, [0], 1, 20_000, 3)) == [4]
+
+
+def test_hand_worked_greedy_replace_lists(cuda_lib):
+    """The certain-edge graphs whose AdvancedGreedy / GreedyReplace lists are worked out by hand
+    (list order, the slot of a replacement, the reverse walk and the early stop of Alg. 4), and
+    the number of sampled graphs each run took (theta per Alg. 2 call up to the stop)."""
+    from tests.test_oracle_greedy_replace import GOLDEN_CASES
+    for name, g, seeds, want in GOLDEN_CASES:
+        gh = cuda_lib.load_graph(g)
+        for alg, b, lst, calls in want:
+            f = cuda_lib.greedy_replace if alg == "GR" else cuda_lib.advanced_greedy
+            assert [int(x) for x in f(gh, seeds, b, 5, 3)] == lst, (name, alg, b)
+            assert cuda_lib.last_stats()["samples"] == 5 * calls, (name, alg, b)
 
 
 @pytest.fixture(scope="module")
@@ -157,14 +170,14 @@ def test_autotune(cuda_lib, monkeypatch):
 
 
 def test_warp_tiers_match_on_full_size_round(cuda_lib, monkeypatch, rmat17):
-    """The warp-tier pipeline (used for graphs above 2^18 vertices) on the bench graph, one
-    call at theta = 20,000, against the block tier's result (which the oracle pins below)."""
+    """The warp-tier pipeline (tiers 0, 1 and 2 without the block tier) and the default pipeline
+    on the bench graph, one call at theta = 20,000 each, both against the oracle."""
     q = rmat17
     gh = cuda_lib.load_graph(q.graph)
-    a = cuda_lib.estimate_decrease(gh, q.seeds, [], 20_000, q.key, 3)
+    want = oracle_pool.decrease(q.graph, q.seeds, [], 20_000, q.key, 3)
+    assert np.array_equal(cuda_lib.estimate_decrease(gh, q.seeds, [], 20_000, q.key, 3), want)
     monkeypatch.setenv("IMIN_DISABLE_CTA_TIER", "1")
-    b = cuda_lib.estimate_decrease(gh, q.seeds, [], 20_000, q.key, 3)
-    assert np.array_equal(a, b)
+    assert np.array_equal(cuda_lib.estimate_decrease(gh, q.seeds, [], 20_000, q.key, 3), want)
 
 
 def test_device_pointers_and_determinism(cuda_lib, tiny):
@@ -293,18 +306,15 @@ def rmat22():
 
 
 def test_rmat22_counters(cuda_lib, rmat22, monkeypatch):
-    """At full graph size: the first 2,000 sampled graphs of a call against the oracle, and a
-    20,000-sample call of the block tier against the warp-tier pipeline (an independent GPU
-    implementation of the same sample routine)."""
+    """At full graph size, 2,000 sampled graphs of round 5 through the default pipeline (block
+    tier with the bitmap in global memory) and through the warp-tier pipeline (per-warp global
+    hash, then whole-graph scratch), both against the oracle."""
     q = rmat22
     gh = cuda_lib.load_graph(q.graph)
-    got = cuda_lib.estimate_decrease(gh, q.seeds, [], 2000, q.key, 0)
-    want = oracle_pool.decrease(q.graph, q.seeds, [], 2000, q.key, 0)
-    assert np.array_equal(got, want)
-    a = cuda_lib.estimate_decrease(gh, q.seeds, [], 20_000, q.key, 5)
+    want = oracle_pool.decrease(q.graph, q.seeds, [], 2000, q.key, 5)
+    assert np.array_equal(cuda_lib.estimate_decrease(gh, q.seeds, [], 2000, q.key, 5), want)
     monkeypatch.setenv("IMIN_DISABLE_CTA_TIER", "1")
-    b = cuda_lib.estimate_decrease(gh, q.seeds, [], 20_000, q.key, 5)
-    assert np.array_equal(a, b)
+    assert np.array_equal(cuda_lib.estimate_decrease(gh, q.seeds, [], 2000, q.key, 5), want)
 
 
 def test_cuda_graph_capture_matches_plain_launches(cuda_lib, tiny, monkeypatch):

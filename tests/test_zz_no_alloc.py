@@ -1,18 +1,27 @@
 """The allocation-free variant of Alg. 2 (imin_estimate_decrease_noalloc) against the regular
-entry point, through the C ABI.
+entry point and the oracle, through the C ABI.
 
-Callers that cannot allocate device memory at call time (stream capture, a foreign allocator
-with a fixed budget, latency-critical paths) use the variant; it must return exactly the
-counters of imin_estimate_decrease. Two calls in a row check that what the static scratch keeps
-from the previous call never leaks into the next. This file is collected last so that a run that
-stops at the first failure has already run every other test.
+Callers that cannot allocate device memory at call time (a foreign allocator with a fixed
+budget, latency-critical paths where cudaMalloc/cudaFree may synchronize the device) use the
+variant; it must return exactly the counters of imin_estimate_decrease. Two calls in a row check
+that what the static scratch keeps from the previous call never leaks into the next. This file
+is collected last so that a run that stops at the first failure has already run every other
+test.
 """
 from __future__ import annotations
+
+import os
+import subprocess
+import sys
+import textwrap
 
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2302_13529_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 pytestmark = pytest.mark.gpu
 
@@ -27,6 +36,7 @@ def test_no_alloc_matches_regular_entry_point(cuda_lib):
         want = cuda_lib.estimate_decrease(gh, q.seeds, bl, theta, q.key, rnd)
         got = cuda_lib.estimate_decrease_noalloc(gh, q.seeds, bl, theta, q.key, rnd)
         assert np.array_equal(got, want), rnd  # integer counters: tolerance 0
+        assert np.array_equal(got, O.decrease(q.graph, q.seeds, bl, theta, q.key, rnd)), rnd
     # device-resident inputs and output, twice in a row
     seeds_d = torch.from_numpy(q.seeds).cuda()
     out = torch.empty(q.graph.n, dtype=torch.uint64, device="cuda")
@@ -52,3 +62,45 @@ def test_no_alloc_rejects_requests_beyond_its_limits(cuda_lib):
     with pytest.raises(IminError) as e:
         cuda_lib.estimate_decrease_noalloc(gh, [int(q.seeds[0])] * 2, [], 10, 1, 0)
     assert e.value.code == -1
+
+
+_CAPACITY_CHILD = textwrap.dedent("""
+    import sys
+    sys.path.insert(0, {root!r})
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2302_13529_gb300 import imin, workloads as W
+    torch.cuda.set_device(0)
+    g = W.graph_rmat_wc(11, 16000, seed=5)
+    seeds = W.uniform_seeds(g.n, 12, seed=6)
+    gh = imin.load_graph(g)
+    try:
+        imin.estimate_decrease_noalloc(gh, seeds, [], 3000, 1234, 2)
+        print("no error")
+        sys.exit(1)
+    except imin.IminError as e:
+        assert e.code == -4, e
+    # the regular entry point hands the same samples to its whole-graph tier
+    assert np.array_equal(imin.estimate_decrease(gh, seeds, [], 3000, 1234, 2),
+                          O.decrease(g, seeds, [], 3000, 1234, 2))
+    # the next call after the failure: an out-tree has no non-tree edges, so it fits
+    rng = np.random.default_rng(3)
+    parent = [int(rng.integers(0, v)) for v in range(1, 500)]
+    t = W.graph_from_edges(500, [(p, v + 1, W.Fraction(1, 2)) for v, p in enumerate(parent)])
+    th = imin.load_graph(t)
+    got = imin.estimate_decrease_noalloc(th, [0], [], 4000, 99, 1)
+    assert np.array_equal(got, imin.estimate_decrease(th, [0], [], 4000, 99, 1))
+    assert np.array_equal(got, O.decrease(t, [0], [], 4000, 99, 1))
+    print("capacity ok")
+""")
+
+
+def test_no_alloc_capacity_error_then_next_call(cuda_lib):
+    """IMIN_ERR_CAPACITY when a sample needs more non-tree edges than the block tier holds (the
+    IMIN_CTA_EDGE_CAP hook, set before the first call of a fresh process because the launch plan
+    is kept per graph size), and a correct call right after it."""
+    env = dict(os.environ, IMIN_CTA_EDGE_CAP="2", IMIN_TIER0_VERTICES="0")
+    r = subprocess.run([sys.executable, "-c", _CAPACITY_CHILD.format(root=ROOT)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "capacity ok" in r.stdout, r.stdout + r.stderr
