@@ -1,17 +1,23 @@
 #!/usr/bin/env python
 """Throughput benchmark of the GB300 sampled-dominator-tree estimator.
 
-A step is one AdvancedGreedy query (Alg. 3): b rounds, each one Alg. 2 call over theta sampled
-graphs (live-edge decisions, BFS from the seeds, dominator tree, subtree sizes, counter
-update) followed by the blocker selection. Workload: R-MAT n=2^17, m=2^20 (a,b,c,d =
-.57/.19/.19/.05), weighted-cascade thresholds, |S|=50 uniform seeds, b=50, theta=10^5.
+Headline (value): a step is one AdvancedGreedy query (Alg. 3) on the mid-scale workload -- R-MAT
+n=2^17, m=2^20 (a,b,c,d = .57/.19/.19/.05), weighted-cascade thresholds, |S|=50 uniform seeds,
+b=50, theta=10^5: b rounds, each one Alg. 2 call over theta sampled graphs (live-edge decisions,
+BFS from the seeds, dominator tree, subtree sizes, counter update) followed by the blocker
+selection, all rounds in one captured CUDA graph (the production path). value = sampled graphs
+per second with the graph and seeds already on the device; e2e = the same metric through the C
+ABI from pinned host buffers, graph upload and blocker read-back included in every step.
 
-value = sampled graphs processed per second (b * theta per step) with the graph and the seed
-set already on the device; e2e = the same metric through the C ABI from pinned host buffers,
-graph upload and blocker read-back included in every step.
+The same line carries the metric's other quantities, each measured in this run (N = 1 only):
+  batched_vs_plain  256 Chung-Lu TR queries in one batched call vs one call per query
+                    (samples/s of both, their ratio, bit-exactness of every result);
+  large_query       R-MAT n=2^22, m=2^26, |S|=200, b=200, theta=2*10^5: AG and GR wall time;
+  serving           a Poisson request stream on the R-MAT 2^17 and 2^22 graphs: p50/p99 latency
+                    and samples/s against serving the same requests one at a time.
 
-Under torchrun (N > 1) every rank runs an independent query replica on its own GPU (the path
-has no exchange step); value = samples of all ranks / the slowest rank's time.
+Under torchrun (N > 1) every rank runs an independent replica of the headline query on its own
+GPU (the path has no exchange step); value = samples of all ranks / the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -36,6 +42,8 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+SAMPLE_KINDS = (("sample_tier0", 0, "k_sample_tier0"), ("sample_tier1", 1, "k_sample_tier1"),
+                ("sample_tier2", 2, "k_sample_tier2"), ("sample_cta", 3, "k_sample_cta"))
 
 
 def parse_args(argv=None):
@@ -46,16 +54,16 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="headline only: skip the batched, large-query and serving legs")
     p.add_argument("--ref-step-seconds", type=float, default=10.0,
                    help="--impl reference: target host time of one step (a bounded sample)")
-    p.add_argument("--cpu-seconds", type=float, default=15.0,
-                   help="target CPU time of the oracle baseline sample")
+    p.add_argument("--cpu-seconds", type=float, default=10.0,
+                   help="target CPU time of each oracle baseline sample")
     p.add_argument("--workload", choices=("rmat17", "batch256", "serving", "rmat22"), default="rmat17",
-                   help="rmat17: one AdvancedGreedy query on R-MAT 2^17 (the headline line); "
-                        "batch256: 256 Chung-Lu/TR queries, batched vs one query per launch; "
-                        "serving: Poisson request stream on the R-MAT 2^17 and 2^22 graphs; "
-                        "rmat22: AG and GR wall time of the large single query (R-MAT 2^22)")
-    p.add_argument("--requests", type=int, default=30,
+                   help="rmat17: the full line (headline plus the other legs); batch256, serving, "
+                        "rmat22: one leg alone, printed as its own line")
+    p.add_argument("--requests", type=int, default=16,
                    help="serving: number of requests (the full configuration has 2,000)")
     p.add_argument("--b", type=int, default=None,
                    help="rmat22: budget override (smaller cases for profiling; default 200)")
@@ -150,14 +158,28 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def gpu_index(local_rank: int) -> int:
+    first = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    return int(first) if first.isdigit() else local_rank
+
+
 # --------------------------------------------------------------------------------------------
 # roofline accounting
 # --------------------------------------------------------------------------------------------
 
 def algorithmic_bytes(stats: dict, tier: int, n_seeds: int) -> float:
-    """Bytes the method must move for the samples finished by one kernel tier:
-    8|R| (row offsets of every reached vertex) + 4 E_R (threshold of every examined edge)
-    + 4 L (target of every live edge) + 8 |R \\ S| (one uint64 counter per reached non-seed)."""
+    """Bytes the method must move for the samples one kernel tier finished, per sample
+    8|R| (the row-offset pair of every reached vertex) + 8 E_R (target and threshold of every
+    examined edge) + 8 |R \\ S| (one uint64 counter update per reached non-seed)."""
+    r = stats["tier_reached"][tier]
+    e = stats["tier_examined_edges"][tier]
+    s = stats["tier_samples"][tier] * n_seeds
+    return 8.0 * r + 8.0 * e + 8.0 * (r - s)
+
+
+def algorithmic_bytes_live_targets(stats: dict, tier: int, n_seeds: int) -> float:
+    """The same with a target read only for live edges (how the kernels read the graph):
+    8|R| + 4 E_R + 4 L + 8 |R \\ S|."""
     r = stats["tier_reached"][tier]
     e = stats["tier_examined_edges"][tier]
     l_ = stats["tier_live_edges"][tier]
@@ -177,62 +199,135 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
-    current kernel sources (profiles/<kernel>_<workload>.md: 'source_hash:' and
-    'dram_bytes_per_launch:' lines); None otherwise."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{WORKLOAD}.md")
+def profile_fields(kernel: str, workload: str = WORKLOAD) -> dict:
+    """'key: value' header lines of the committed ncu summary profiles/<kernel>_<workload>.md."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
-        return None
-    src, val = None, None
+        return {}
+    out = {}
     for line in open(path):
-        if line.startswith("source_hash:"):
-            src = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_launch:"):
-            val = float(line.split(":", 1)[1].strip())
-    return val if src == kernel_source_hash() else None
+        if ":" in line and not line.startswith(("#", "|", " ", "*", "`")):
+            k, v = line.split(":", 1)
+            out[k.strip()] = v.strip()
+    return out
+
+
+def ncu_traffic(kernel: str, workload: str = WORKLOAD):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
+    current kernel sources ('source_hash:' and 'dram_bytes_per_launch:' lines); None otherwise."""
+    f = profile_fields(kernel, workload)
+    if f.get("source_hash") != kernel_source_hash() or "dram_bytes_per_launch" not in f:
+        return None
+    return float(f["dram_bytes_per_launch"])
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
+
+
+def roofline_of(prof: dict, stats: dict, n_seeds: int, workload: str = WORKLOAD) -> dict:
+    """Roofline of the sample kernel with the most device time: algorithmic bytes per launch
+    (from the kernels' own work counters) over its average CUDA-event launch time, against the
+    measured HBM copy bandwidth. `bound` names what limits the kernel: HBM when its DRAM traffic
+    (ncu) is of the order of the algorithmic bytes, instruction issue when the graph is served
+    from L2 (DRAM traffic far below the algorithmic bytes)."""
+    kind, tier, kname = max(SAMPLE_KINDS, key=lambda k: prof[k[0]]["ms"])
+    kp = prof[kind]
+    launches = max(kp["launches"], 1)
+    avg_ms = kp["ms"] / launches
+    alg = algorithmic_bytes(stats, tier, n_seeds) / launches
+    alg_live = algorithmic_bytes_live_targets(stats, tier, n_seeds) / launches
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = alg / (avg_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(kname, workload)
+    fields = profile_fields(kname, workload)
+    bound = "hbm"
+    if traffic is not None and traffic < 0.25 * alg:
+        bound = "issue"
+    total = sum(v["ms"] for v in prof.values())
+    out = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak,
+           "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
+           "frac_of": f"{src} HBM copy bandwidth", "traffic": traffic,
+           "algorithmic_bytes_per_launch": alg,
+           "algorithmic_bytes_per_launch_live_targets": alg_live,
+           "frac_live_targets": alg_live / (avg_ms * 1e-3) / 1e9 / peak,
+           "avg_launch_ms": avg_ms, "launches": kp["launches"],
+           "share_of_device_time": kp["ms"] / max(total, 1e-9),
+           "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
+    if "issue_active_pct" in fields and fields.get("source_hash") == kernel_source_hash():
+        out["issue_active_pct"] = float(fields["issue_active_pct"])
+    return out
+
+
+def sum_stats(acc, st):
+    if acc is None:
+        return {k: (list(v) if isinstance(v, list) else v) for k, v in st.items()}
+    for k, v in st.items():
+        acc[k] = [a + b for a, b in zip(acc[k], v)] if isinstance(v, list) else acc[k] + v
+    return acc
 
 
 # --------------------------------------------------------------------------------------------
-# arms
+# CPU baselines and the reference arm (the oracle as it stands, on the host cores)
 # --------------------------------------------------------------------------------------------
+
+def _oracle_rate(q, threads: int, seconds: float):
+    from oracle import oracle as O
+
+    with O.threads(threads):
+        probe = 100 * threads
+        t = time.perf_counter()
+        O.decrease(q.graph, q.seeds, [], probe, q.key, 0)
+        per = (time.perf_counter() - t) / probe
+        count = int(max(probe, min(q.theta, seconds / max(per, 1e-8))))
+        t = time.perf_counter()
+        O.decrease(q.graph, q.seeds, [], count, q.key, 0)
+        dt = time.perf_counter() - t
+    return count / dt, count, dt
+
 
 def cpu_baseline(q, seconds: float):
-    """The oracle as it stands (single-threaded C), on a bounded sample of the workload:
-    the first `count` sampled graphs of round 0, sized to take about `seconds`."""
+    """The oracle as it stands on a bounded sample of the workload (the first `count` sampled
+    graphs of round 0, sized to take about `seconds`): on all host cores (its thread-parallel
+    sample loop) and on one core."""
     from oracle import oracle as O
 
     O.lib()
-    t = time.perf_counter()
-    O.decrease(q.graph, q.seeds, [], 200, q.key, 0)
-    per = (time.perf_counter() - t) / 200
-    count = int(max(200, min(q.theta, seconds / max(per, 1e-7))))
-    t = time.perf_counter()
-    O.decrease(q.graph, q.seeds, [], count, q.key, 0)
-    dt = time.perf_counter() - t
-    return {"value": count / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": f"round 0, samples 0..{count - 1} of theta={q.theta} ({dt:.1f} s)"}
+    cores = os.cpu_count() or 1
+    v_all, c_all, t_all = _oracle_rate(q, cores, seconds)
+    v_one, c_one, t_one = _oracle_rate(q, 1, seconds)
+    return {"value": v_all, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"round 0, samples 0..{c_all - 1} of theta={q.theta} ({t_all:.1f} s, "
+                      f"{cores} threads)",
+            "single_core": {"value": v_one, "cores": 1,
+                            "sample": f"round 0, samples 0..{c_one - 1} ({t_one:.1f} s)"}}
 
 
 def run_reference(args, q, rank):
-    """The oracle timed on the host cores on the same workload, metric and unit; each step is a
+    """The oracle timed on all host cores on the same workload, metric and unit; each step is a
     bounded sample (a range of sampled graphs of one round)."""
     from oracle import oracle as O
 
     if rank != 0:
         return
     O.lib()
-    t = time.perf_counter()
-    O.decrease(q.graph, q.seeds, [], 100, q.key, 0)
-    per = (time.perf_counter() - t) / 100
-    per_step = int(max(100, min(q.theta, args.ref_step_seconds / max(per, 1e-7))))
-    for w in range(args.warmup):
-        O.decrease(q.graph, q.seeds, [], min(per_step, 200), q.key, w)
-    times = []
-    for k in range(args.steps):
+    cores = os.cpu_count() or 1
+    with O.threads(cores):
         t = time.perf_counter()
-        O.decrease(q.graph, q.seeds, [], per_step, q.key, k, (k * per_step) % q.theta)
-        times.append(time.perf_counter() - t)
+        O.decrease(q.graph, q.seeds, [], 50 * cores, q.key, 0)
+        per = (time.perf_counter() - t) / (50 * cores)
+        per_step = int(max(100, min(q.theta, args.ref_step_seconds / max(per, 1e-8))))
+        for w in range(args.warmup):
+            O.decrease(q.graph, q.seeds, [], min(per_step, 200), q.key, w)
+        times = []
+        for k in range(args.steps):
+            t = time.perf_counter()
+            O.decrease(q.graph, q.seeds, [], per_step, q.key, k, (k * per_step) % q.theta)
+            times.append(time.perf_counter() - t)
     total = sum(times)
     value = per_step * args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
@@ -240,8 +335,9 @@ def run_reference(args, q, rank):
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "uint32", "data": "synthetic",
             "config": config_of(q),
-            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} sampled graphs of one round per step"},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} sampled graphs of one round per step, "
+                                       f"{cores} threads"},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -254,87 +350,84 @@ def config_of(q):
             "l2": "flushed between steps (512 MiB write outside the step events)"}
 
 
-def run_batch(args, rank, world, dist):
+# --------------------------------------------------------------------------------------------
+# legs
+# --------------------------------------------------------------------------------------------
+
+def leg_batch(steps: int, warmup: int, key_offset: int = 0) -> dict:
     """256 independent AdvancedGreedy queries (Chung-Lu, n log-uniform in [1e3, 2e5], mean degree
-    U[5,20], TR probabilities, |S| U[5,100], b=20, theta=2e4): one batched call (a step) vs the
-    same queries one imin_advanced_greedy call at a time; the results must be identical."""
+    U[5,20], TR probabilities, |S| U[5,100], b=20, theta=2e4): one batched call per step vs the
+    same queries one imin_advanced_greedy call at a time (cutoffs tuned before timing); every
+    result must be identical."""
     import numpy as np
     import torch
-    from paper_2302_13529_gb300 import build, imin, workloads as W
+    from paper_2302_13529_gb300 import imin, workloads as W
 
-    build.build()
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     t0 = time.perf_counter()
     qs = W.batch_queries(256)
     gen_s = time.perf_counter() - t0
     hs = [imin.load_graph(q.graph) for q in qs]
-    items = [(h, q.seeds, q.b, q.theta, q.key + rank) for h, q in zip(hs, qs)]
+    items = [(h, q.seeds, q.b, q.theta, q.key + key_offset) for h, q in zip(hs, qs)]
     samples = sum(q.b * q.theta for q in qs)  # every query runs b rounds (n - |S| >= b here)
-    for _ in range(max(args.warmup, 3) if args.warmup else 1):
+    for _ in range(max(warmup, 1)):
         imin.batch_advanced_greedy(items)
     torch.cuda.synchronize()
-    imin.profile_read(reset=True)
-    imin.profile_enable(True)
     launches0 = imin.launch_count()
     times = []
     res = None
-    for _ in range(args.steps):
+    for _ in range(steps):
         torch.cuda.synchronize()
         t = time.perf_counter()
         res = imin.batch_advanced_greedy(items)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t)
     launches = imin.launch_count() - launches0
+    st = imin.last_stats()
+    imin.profile_read(reset=True)
+    imin.profile_enable(True)
+    imin.batch_advanced_greedy(items)
     imin.profile_enable(False)
     prof = imin.profile_read(reset=True)
-    st = imin.last_stats()
-    for h, q in zip(hs, qs):  # the plain calls' per-graph cutoff tuning stays out of their timing
-        imin.autotune(h, q.seeds, q.key + rank)
+    for h, it in zip(hs, items):  # the plain calls' per-graph cutoff tuning stays out of their timing
+        imin.autotune(h, it[1], it[4])
+    imin.advanced_greedy(*items[0])
     torch.cuda.synchronize()
     t = time.perf_counter()
     plain = [imin.advanced_greedy(*it) for it in items]
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t
     same = all(np.array_equal(a, b) for a, b in zip(res, plain))
-    batched_s = sum(times) / len(times)
-    line = {"metric": METRIC, "value": samples / batched_s, "unit": "samples/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * batched_s,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "uint32",
-            "data": "synthetic",
-            "config": {"workload": "batch256-chunglu-tr-advanced-greedy", "queries": len(qs),
-                       "b": 20, "theta": 20000, "samples_per_step": samples,
-                       "total_edges": int(sum(q.graph.m for q in qs)),
-                       "generation_s": round(gen_s, 1)},
+    batched_s = min(times)
+    for h in hs:
+        h.close()
+    return {"workload": "batch256-chunglu-tr-advanced-greedy", "queries": len(qs), "b": 20,
+            "theta": 20000, "samples_per_call": samples,
+            "total_edges": int(sum(q.graph.m for q in qs)), "generation_s": round(gen_s, 1),
+            "batched": {"value": samples / batched_s, "unit": "samples/s", "seconds": batched_s,
+                        "calls": steps, "gpu_launches_per_call": launches / max(steps, 1)},
             "one_query_per_launch": {"value": samples / plain_s, "unit": "samples/s",
-                                     "seconds": plain_s,
-                                     "cutoff": "autotuned per graph before timing"},
-            "batched_cutoff": int(os.environ.get("IMIN_TIER0_VERTICES", "96") or 96),
+                                     "seconds": plain_s, "cutoff": "autotuned per graph before timing"},
             "batched_over_plain": plain_s / batched_s, "bit_exact_vs_plain": same,
-            "gpu_launches": launches,
             "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
             "work": {"reached_per_sample": st["reached"] / max(st["samples"], 1),
                      "examined_edges_per_sample": st["examined_edges"] / max(st["samples"], 1)}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
 
 
-def run_rmat22(args, rank, world):
+def leg_rmat22(b=None, theta=None, key_offset: int = 0) -> dict:
     """The large single query: R-MAT n=2^22, m=2^26, WC, |S|=200, b=200, theta=2*10^5, rounds
-    captured in one CUDA graph. One AdvancedGreedy query is the step (4*10^7 sampled graphs);
-    the warm-up is one 2-round query (module load, cutoff tuning, allocator pools). GreedyReplace
-    is timed once after it. Inputs are resident on the device."""
+    captured in one CUDA graph, inputs resident on the device. Warm-up: one 2-round query (module
+    load, cutoff tuning, allocator pools); then one AdvancedGreedy and one GreedyReplace query,
+    each timed with CUDA events on the launching stream."""
     import torch
-    from paper_2302_13529_gb300 import build, imin, workloads as W
+    from paper_2302_13529_gb300 import imin, workloads as W
 
-    build.build()
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     t0 = time.perf_counter()
     q = W.rmat22_query()
-    if args.b is not None or args.theta is not None:
-        q = W.Query(q.graph, q.seeds, args.b if args.b is not None else q.b,
-                    args.theta if args.theta is not None else q.theta, q.key)
+    if b is not None or theta is not None:
+        q = W.Query(q.graph, q.seeds, b if b is not None else q.b, theta if theta is not None else q.theta,
+                    q.key)
     gen_s = time.perf_counter() - t0
-    key = q.key + rank
+    key = q.key + key_offset
     gh = imin.load_graph(q.graph)
     seeds_d = torch.from_numpy(q.seeds).cuda()
     out_d = torch.empty(q.b, dtype=torch.int32, device="cuda")
@@ -354,52 +447,36 @@ def run_rmat22(args, rank, world):
         walls[name + "_stats"] = imin.last_stats()
     st = walls["ag_stats"]
     samples = st["samples"]
-    line = {"metric": METRIC, "value": samples / walls["ag"], "unit": "samples/s", "n_gpus": world,
-            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * walls["ag"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "uint32", "data": "synthetic",
-            "config": {"workload": "rmat22-wc-advanced-greedy", "n": q.graph.n, "m": q.graph.m,
-                       "seeds": len(q.seeds), "b": q.b, "theta": q.theta,
-                       "warp_block_cutoff": cutoff, "generation_s": round(gen_s, 1),
-                       "l2": "graph (528 MB) larger than L2"},
+    gh.close()
+    return {"workload": "rmat22-wc", "n": q.graph.n, "m": q.graph.m, "seeds": len(q.seeds),
+            "b": q.b, "theta": q.theta, "warp_block_cutoff": cutoff,
+            "generation_s": round(gen_s, 1), "l2": "graph (528 MB) larger than L2",
             "ag_wall_s": walls["ag"], "gr_wall_s": walls["gr"],
+            "ag_samples_per_s": samples / walls["ag"], "ag_samples": samples,
             "gr_samples": walls["gr_stats"]["samples"],
-            "work": {"reached_per_sample": st["reached"] / samples,
-                     "examined_edges_per_sample": st["examined_edges"] / samples,
+            "work": {"reached_per_sample": st["reached"] / max(samples, 1),
+                     "examined_edges_per_sample": st["examined_edges"] / max(samples, 1),
                      "tier_samples": st["tier_samples"]}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
 
 
-def run_serving(args, rank, world):
+def leg_serving(requests: int, seed: int = 5000) -> dict:
     """Requests against the R-MAT 2^17 (m=2^20) and R-MAT 2^22 (m=2^26) WC graphs held resident:
     each picks a graph with probability 1/2, |S| ~ U[10, 500], b ~ U[10, 100],
-    theta ~ U[1e4, 1e5] (AdvancedGreedy). Phase 1 submits all requests at once to measure the
-    saturation rate; phase 2 replays them with Poisson arrivals at 80 % of that rate and reports
-    p50/p99 latency and throughput; the serial baseline runs a subset one query at a time."""
+    theta ~ U[1e4, 1e5] (AdvancedGreedy). A burst (all requests at once) measures the saturation
+    rate; a replay with Poisson arrivals at 80 % of that rate gives p50/p99 latency and samples/s;
+    the serial baseline runs every third request one query at a time."""
     import threading
 
     import numpy as np
     import torch
-    from paper_2302_13529_gb300 import build, imin, workloads as W
+    from paper_2302_13529_gb300 import imin, workloads as W
 
-    build.build()
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    g17 = W.rmat17_query().graph
-    g22 = W.rmat22_query().graph
-    graphs = [g17, g22]
+    graphs = [W.rmat17_query().graph, W.rmat22_query().graph]
     hs = [imin.load_graph(g) for g in graphs]
-    rng = np.random.default_rng(5000 + rank)
-    reqs = []
-    for i in range(args.requests):
-        gi = int(rng.integers(0, 2))
-        k = int(rng.integers(10, 501))
-        reqs.append((gi, W.uniform_seeds(graphs[gi].n, k, int(rng.integers(1 << 30))),
-                     int(rng.integers(10, 101)), int(rng.integers(10_000, 100_001)),
-                     int(rng.integers(1 << 62))))
-    samples = sum(b * t for _, _, b, t, _ in reqs)
+    reqs = W.serving_requests(requests, seed)
+    samples = sum(r.b * r.theta for r in reqs)
 
     def serve(arrivals):
-        """Submit reqs[:len(arrivals)] at the given offsets (s); return (elapsed, latencies, stats)."""
         todo = reqs[:len(arrivals)]
         lat = [None] * len(todo)
         with imin.Server() as srv:
@@ -407,17 +484,17 @@ def run_serving(args, rank, world):
             tickets = [None] * len(todo)
 
             def submitter():
-                for i, (gi, s, b, t, k) in enumerate(todo):
+                for i, r in enumerate(todo):
                     wait = arrivals[i] - (time.perf_counter() - t0)
                     if wait > 0:
                         time.sleep(wait)
-                    tickets[i] = srv.submit(0, hs[gi], s, b, t, k)
+                    tickets[i] = srv.submit(0, hs[r.gi], r.seeds, r.b, r.theta, r.key)
 
             th = threading.Thread(target=submitter)
             th.start()
             th.join()
-            for i, (gi, s, b, t, k) in enumerate(todo):
-                _, lat[i] = srv.wait(tickets[i], capacity=b)
+            for i, r in enumerate(todo):
+                _, lat[i] = srv.wait(tickets[i], capacity=r.b)
             elapsed = time.perf_counter() - t0
             st = srv.stats()
         return elapsed, np.array(lat), st
@@ -425,24 +502,26 @@ def run_serving(args, rank, world):
     serve([0.0] * min(len(reqs), 2))  # warm-up (module load, first plans)
     burst_s, burst_lat, _ = serve([0.0] * len(reqs))
     rate = 0.8 * len(reqs) / burst_s  # requests per second at 80 % of saturation
-    gaps = np.random.default_rng(6000 + rank).exponential(1.0 / rate, size=len(reqs))
+    gaps = np.random.default_rng(seed + 1000).exponential(1.0 / rate, size=len(reqs))
     poisson_s, lat, st = serve(list(np.cumsum(gaps) - gaps[0]))
-    # serial baseline: one query at a time on a subset (about a third of the requests)
     sub_ids = list(range(0, len(reqs), 3))
+    for i in sub_ids:  # the plain calls' cutoff tuning (per seed-set size class) stays out of their timing
+        r = reqs[i]
+        imin.advanced_greedy(hs[r.gi], r.seeds, 1, 1000, r.key)
+    torch.cuda.synchronize()
     t = time.perf_counter()
     for i in sub_ids:
-        gi, s, b, th_, k = reqs[i]
-        imin.advanced_greedy(hs[gi], s, b, th_, k)
+        r = reqs[i]
+        imin.advanced_greedy(hs[r.gi], r.seeds, r.b, r.theta, r.key)
     torch.cuda.synchronize()
     serial_s = time.perf_counter() - t
-    serial_samples = sum(reqs[i][2] * reqs[i][3] for i in sub_ids)
-    line = {"metric": METRIC, "value": samples / poisson_s, "unit": "samples/s", "n_gpus": world,
-            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * poisson_s, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "uint32", "data": "synthetic",
-            "config": {"workload": "serving-rmat17-rmat22-advanced-greedy",
-                       "requests": len(reqs), "full_configuration_requests": 2000,
-                       "arrivals": f"Poisson at 80% of the burst rate ({rate:.3f} req/s)",
-                       "samples": samples},
+    serial_samples = sum(reqs[i].b * reqs[i].theta for i in sub_ids)
+    for h in hs:
+        h.close()
+    return {"workload": "serving-rmat17-rmat22-advanced-greedy", "requests": len(reqs),
+            "full_configuration_requests": 2000,
+            "arrivals": f"Poisson at 80% of the burst rate ({rate:.3f} req/s)", "samples": samples,
+            "value": samples / poisson_s, "unit": "samples/s", "seconds": poisson_s,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
             "burst": {"seconds": burst_s, "samples_per_s": samples / burst_s,
@@ -450,10 +529,27 @@ def run_serving(args, rank, world):
                       "p99_ms": float(np.percentile(burst_lat, 99))},
             "serial_one_query_at_a_time": {"value": serial_samples / serial_s, "unit": "samples/s",
                                            "requests": len(sub_ids)},
+            "poisson_over_serial": (samples / poisson_s) / (serial_samples / serial_s),
             "server": st}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
 
+
+def leg_line(name: str, leg: dict, world: int) -> dict:
+    """A leg run alone (--workload batch256 / rmat22 / serving), as its own bench line."""
+    if name == "batch256":
+        v, ms = leg["batched"]["value"], 1e3 * leg["batched"]["seconds"]
+    elif name == "rmat22":
+        v, ms = leg["ag_samples_per_s"], 1e3 * leg["ag_wall_s"]
+    else:
+        v, ms = leg["value"], 1e3 * leg["seconds"]
+    return {"metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": world, "steps": 1,
+            "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "uint32", "data": "synthetic",
+            "config": {"workload": leg["workload"]}, name: leg}
+
+
+# --------------------------------------------------------------------------------------------
+# main
+# --------------------------------------------------------------------------------------------
 
 def main(argv=None):
     args = parse_args(argv)
@@ -462,8 +558,8 @@ def main(argv=None):
 
     dist = None
     if world > 1:
-        import torch.distributed as tdist
         import torch
+        import torch.distributed as tdist
         if args.impl == "ours" and torch.cuda.is_available():
             torch.cuda.set_device(local_rank)
             tdist.init_process_group("nccl")
@@ -471,15 +567,6 @@ def main(argv=None):
             tdist.init_process_group("gloo")
         dist = tdist
 
-    if args.workload == "batch256":
-        run_batch(args, rank, world, dist)
-        return
-    if args.workload == "serving":
-        run_serving(args, rank, world)
-        return
-    if args.workload == "rmat22":
-        run_rmat22(args, rank, world)
-        return
     q = W.rmat17_query()
     if args.impl == "reference":
         run_reference(args, q, rank)
@@ -494,6 +581,14 @@ def main(argv=None):
 
     build.build()
     torch.cuda.set_device(local_rank)
+    if args.workload != "rmat17":
+        leg = {"batch256": lambda: leg_batch(max(args.steps, 1), args.warmup, rank),
+               "rmat22": lambda: leg_rmat22(args.b, args.theta, rank),
+               "serving": lambda: leg_serving(args.requests, 5000 + rank)}[args.workload]()
+        if rank == 0:
+            print(json.dumps(leg_line(args.workload, leg, world)), flush=True)
+        return
+
     dev = torch.device("cuda", local_rank)
     key = q.key + rank  # independent replica per rank
     gh = imin.load_graph(q.graph)
@@ -513,6 +608,8 @@ def main(argv=None):
     torch.cuda.synchronize()
     reduce_max, reduce_sum = make_reducers(dist)
 
+    # timed steps: the production path (all rounds of a query in one captured CUDA graph); the
+    # per-kernel events are event-record nodes inside each graph, on the stream it runs on
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     imin.profile_read(reset=True)
@@ -522,21 +619,13 @@ def main(argv=None):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0])
-                      if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit()
-                      else local_rank) as clk:
+    with ClockSampler(gpu_index(local_rank)) as clk:
         for k in range(args.steps):
             flush.fill_(float(k))
             starts[k].record(stream)
             step()
             stops[k].record(stream)
-            st = imin.last_stats()
-            if stats_sum is None:
-                stats_sum = st
-            else:
-                for kk, vv in st.items():
-                    stats_sum[kk] = ([a + b for a, b in zip(stats_sum[kk], vv)]
-                                     if isinstance(vv, list) else stats_sum[kk] + vv)
+            stats_sum = sum_stats(stats_sum, imin.last_stats())
         torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -548,29 +637,20 @@ def main(argv=None):
     samples_local = q.b * q.theta * args.steps
     value, slowest = aggregate(local_s, samples_local, world, reduce_max, reduce_sum)
     ms_per_step = 1e3 * slowest / args.steps
-
-    # roofline of the dominant kernel (the sample tier with the most device time)
-    tiers = [("sample_tier0", 0), ("sample_tier1", 1), ("sample_tier2", 2), ("sample_cta", 3)]
-    kname, tier = max(tiers, key=lambda kt: prof[kt[0]]["ms"])
-    kp = prof[kname]
-    avg_ms = kp["ms"] / max(kp["launches"], 1)
-    alg_bytes = algorithmic_bytes(stats_sum, tier, len(q.seeds)) / max(kp["launches"], 1)
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if peak else "fallback"
-    peak = peak or 6800.0
-    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
-    kfn = "k_sample_cta" if tier == 3 else f"k_sample_tier{tier}"
-    traffic = ncu_traffic(kfn)
-    total_ms = sum(v["ms"] for v in prof.values())
-    roofline = {"kernel": kfn, "bound": "hbm", "achieved": achieved,
-                "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
-                "avg_launch_ms": avg_ms, "share_of_device_time": kp["ms"] / max(total_ms, 1e-9),
-                "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
+    roofline = roofline_of(prof, stats_sum, len(q.seeds))
+    if sum(v["ms"] for v in prof.values()) <= 0:
+        # event nodes inside graphs gave no times: time one query with the graphs off instead
+        os.environ["IMIN_NO_GRAPHS"] = "1"
+        imin.profile_enable(True)
+        step()
+        torch.cuda.synchronize()
+        imin.profile_enable(False)
+        del os.environ["IMIN_NO_GRAPHS"]
+        prof = imin.profile_read(reset=True)
+        roofline = roofline_of(prof, imin.last_stats(), len(q.seeds))
+        roofline["timing"] = "separate untimed query without CUDA graphs"
+    else:
+        roofline["timing"] = "CUDA events inside the timed steps' graphs"
 
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
@@ -581,20 +661,24 @@ def main(argv=None):
                      "examined_edges_per_sample": stats_sum["examined_edges"] / stats_sum["samples"],
                      "live_edges_per_sample": stats_sum["live_edges"] / stats_sum["samples"],
                      "live_edges_per_s": value * stats_sum["live_edges"] / stats_sum["samples"],
+                     "examined_edges_per_s": value * stats_sum["examined_edges"] / stats_sum["samples"],
                      "tier_samples": stats_sum["tier_samples"]},
             "ag_wall_s": ms_per_step / 1e3}
     clocks = clk.summary()
     if clocks is not None:
         line["clocks"] = clocks
 
-    # GreedyReplace wall time (one query, device-resident inputs)
+    # GreedyReplace wall time (one query, device-resident inputs, CUDA events)
     ag_blockers = out_d.cpu().numpy().copy()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    t = time.perf_counter()
+    e0.record(stream)
     imin.greedy_replace(gh, seeds_d, q.b, q.theta, key, out=out_d)
+    e1.record(stream)
     torch.cuda.synchronize()
-    line["gr_wall_s"] = time.perf_counter() - t
-    gr_blockers = out_d.cpu().numpy().copy()
+    line["gr_wall_s"] = e0.elapsed_time(e1) / 1e3
+    line["gr_samples"] = imin.last_stats()["samples"]
+    gr_blockers = out_d[:q.b].cpu().numpy().copy()
 
     # quality of the blocker sets: expected spread by simulation (Def. 3), 10^5 sampled graphs
     # on an independent key, as the paper evaluates its results
@@ -625,9 +709,16 @@ def main(argv=None):
         e2e_value, _ = aggregate(e2e_s, q.b * q.theta * e2e_steps, world, reduce_max, reduce_sum)
         line["e2e"] = {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-                       "includes": "graph upload + validation, warp/block cutoff tuning of the "
-                                   "new graph handle, seed upload, 50 rounds, blocker read-back"}
+                       "includes": "graph upload + validation (a new handle each step; its "
+                                   "warp/block cutoff comes from the process-wide tuning cache), "
+                                   "seed upload, 50 rounds in one CUDA graph, blocker read-back"}
+    gh.close()
+    del flush
 
+    if world == 1 and not args.no_extras:
+        line["batched_vs_plain"] = leg_batch(2, 1)
+        line["large_query"] = leg_rmat22()
+        line["serving"] = leg_serving(args.requests)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(q, args.cpu_seconds)
     if rank == 0:

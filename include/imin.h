@@ -63,6 +63,27 @@ typedef struct imin_graph imin_graph;
 int imin_load_graph(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t* col,
                     const uint32_t* thr, void* stream, imin_graph** out);
 
+/* Load a graph under the linear-threshold model, the standard triggering model (Sec. 4.5: every
+ * vertex v draws a triggering set of in-neighbours, and only edges from that set stay). In the
+ * LT model the set holds at most one in-neighbour: in-edge (u, v) with probability b(u, v), none
+ * with probability 1 - sum_u b(u, v).
+ *   weight   uint32[m]: weight[e] + 1 is edge e's share b(u, v) * 2^32 (the same fixed point as
+ *            the IC thresholds, so weight = 0xFFFFFFFF is b = 1). The in-edges of each vertex v,
+ *            in ascending edge id, take consecutive intervals [lo_e, lo_e + weight[e]] of
+ *            [0, 2^32); sample j of call `round` under key K keeps edge e = (u, v) iff v's word --
+ *            word (v & 3) of Philox4x32-10 with counter (v >> 2, j, round, 0x80000000) and the
+ *            key of the IC stream -- lies in e's interval. The shares of one vertex's in-edges
+ *            must sum to at most 2^32.
+ *   Other arguments as for imin_load_graph. Every entry point below accepts the handle and
+ *   computes the same quantities (Alg. 2 counters, AdvancedGreedy, GreedyReplace, batches,
+ *   serving, spread) on the LT sampled graphs.
+ * Errors: as imin_load_graph; IMIN_ERR_INVALID also when some vertex's shares exceed 2^32. */
+int imin_load_graph_lt(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t* col,
+                       const uint32_t* weight, void* stream, imin_graph** out);
+
+/* The propagation model of a loaded graph: 0 = independent cascade, 1 = linear threshold. */
+int imin_graph_model(const imin_graph* g);
+
 /* Release a graph handle and its device memory (after all work using it has finished).
  * NULL is accepted. */
 int imin_free_graph(imin_graph* g);
@@ -285,10 +306,11 @@ int imin_last_stats(imin_stats* out);
 uint64_t imin_launch_count(void);
 
 /* Per-kind kernel timing. When enabled, every kernel launch of the entry points above is
- * bracketed by CUDA events recorded on the stream it is launched on; the elapsed times are
- * added up when the entry point synchronizes. Kinds: 0-3 = sample tiers 0-3, 4 = blocker
- * selection, 5 = other small kernels (only launches of kind 5 made by the greedy drivers are
- * timed). Timing adds event records between launches. */
+ * bracketed by CUDA events recorded on the stream it is launched on -- inside the CUDA graph of
+ * a greedy or batched driver as event-record nodes, so the captured production path is what is
+ * timed; the elapsed times are added up when the entry point synchronizes. Kinds: 0-3 = sample
+ * tiers 0-3, 4 = blocker selection, 5 = other small kernels (only launches of kind 5 made by the
+ * greedy drivers are timed). Timing adds event records between launches. */
 typedef struct imin_profile {
     uint64_t launches[6];
     double ms[6];

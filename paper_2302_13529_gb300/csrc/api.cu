@@ -75,6 +75,17 @@ struct CallTimer {
             cudaEventDestroy(std::get<2>(r));
         }
     }
+    // Record `ev` on the stream. While the stream is being captured into a CUDA graph the record
+    // becomes an event-record node of the graph (cudaEventRecordExternal), so the events time the
+    // kernels each time the graph runs.
+    cudaError_t record(cudaEvent_t ev)
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t e = cudaStreamIsCapturing(s, &cs);
+        if (e != cudaSuccess) return e;
+        if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+        return cudaEventRecord(ev, s);
+    }
     // Enqueue `launch` (returns cudaError_t, sets *launched) bracketed by events.
     template <typename F>
     cudaError_t run(int kind, F&& launch)
@@ -83,14 +94,14 @@ struct CallTimer {
         if (on) {
             cudaError_t e = cudaEventCreate(&a);
             if (e == cudaSuccess) e = cudaEventCreate(&b);
-            if (e == cudaSuccess) e = cudaEventRecord(a, s);
+            if (e == cudaSuccess) e = record(a);
             if (e != cudaSuccess) return e;
         }
         bool launched = false;
         cudaError_t e = launch(&launched);
         if (launched) g_launches.fetch_add(1, std::memory_order_relaxed);
         if (on) {
-            if (e == cudaSuccess && launched) e = cudaEventRecord(b, s);
+            if (e == cudaSuccess && launched) e = record(b);
             recs.emplace_back(launched ? kind : -1, a, b);
         }
         return e;
@@ -114,8 +125,8 @@ struct CallTimer {
 
 // Captures the launches of a driver's rounds into one CUDA graph and launches it. Capture runs on
 // a private stream that first waits for the caller's stream (the legacy default stream cannot be
-// captured); the caller's stream then waits for the graph. Disabled while per-kernel profiling
-// is on (events between launches) and by IMIN_NO_GRAPHS=1.
+// captured); the caller's stream then waits for the graph. Per-kernel profiling events become
+// event-record nodes of the graph. Disabled by IMIN_NO_GRAPHS=1.
 struct GraphScope {
     cudaStream_t user = nullptr, cap = nullptr;
     cudaEvent_t ev = nullptr;
@@ -126,7 +137,7 @@ struct GraphScope {
     static bool enabled()
     {
         const char* v = std::getenv("IMIN_NO_GRAPHS");
-        return !(v && *v && *v != '0') && g_profile_on.load() == 0;
+        return !(v && *v && *v != '0');
     }
     cudaError_t begin(cudaStream_t s)
     {
@@ -240,11 +251,6 @@ int check_ids(const std::vector<int32_t>& ids, int32_t n, std::vector<uint8_t>& 
         mark[v] = tag;
     }
     return IMIN_OK;
-}
-
-DevGraph dev_graph(const imin_graph* g)
-{
-    return DevGraph{g->n, g->m, g->row_ptr, g->col, g->thr4};
 }
 
 // Everything one query needs on the device besides its graph.
@@ -732,7 +738,6 @@ int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t
         }
         IMIN_CUDA(G.begin(s));
         T.s = G.stream();
-        T.on = T.on && !G.on;
         for (int32_t i = 0; i < count; ++i) {
             const SampleParams P = sample_params(g, q, n_seeds, theta, key, static_cast<uint32_t>(i),
                                                  ctl + i, nullptr);
@@ -762,7 +767,6 @@ int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t
         }
         IMIN_CUDA(G.begin(s));
         T.s = G.stream();
-        T.on = T.on && !G.on;
         const cudaStream_t rs = G.stream();
         uint32_t round = 0;
         // phase 1: greedy over the seeds' out-neighbours
@@ -1009,7 +1013,6 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
     GraphScope G;
     IMIN_CUDA(G.begin(s));
     T.s = G.stream();
-    T.on = T.on && !G.on;
     const cudaStream_t rs = G.stream();
     for (int32_t c = 0; c < steps; ++c) {
         BatchStep B{};
@@ -1092,10 +1095,16 @@ int imin_abi_version(void) { return IMIN_ABI_VERSION; }
 
 const char* imin_last_error(void) { return g_err; }
 
-int imin_load_graph(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t* col,
-                    const uint32_t* thr, void* stream, imin_graph** out)
+}  // extern "C"
+
+namespace {
+
+// Graph upload shared by the IC and LT loaders. model 1 (LT): thr[e] + 1 is edge e's share of
+// 2^32; the in-edges of each vertex take consecutive intervals in ascending edge id, whose starts
+// are computed here, and the shares of one vertex must not exceed 2^32.
+int load_impl(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t* col, const uint32_t* thr,
+              int32_t model, void* stream, imin_graph** out)
 {
-    g_err[0] = '\0';
     if (out == nullptr) return fail(IMIN_ERR_INVALID, "out is NULL");
     *out = nullptr;
     if (n <= 0) return fail(IMIN_ERR_INVALID, "n must be > 0");
@@ -1112,13 +1121,26 @@ int imin_load_graph(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t*
         if (hrp[u + 1] < hrp[u]) return fail(IMIN_ERR_INVALID, "row_ptr must be non-decreasing");
     for (int64_t e = 0; e < m; ++e)
         if (hcol[e] < 0 || hcol[e] >= n) return fail(IMIN_ERR_INVALID, "col entry out of range");
+    std::vector<uint32_t> hlo;
+    if (model == 1) {
+        std::vector<uint64_t> acc(static_cast<size_t>(n), 0);
+        hlo.resize(static_cast<size_t>(m));
+        for (int64_t e = 0; e < m; ++e) {
+            uint64_t& a = acc[static_cast<size_t>(hcol[e])];
+            hlo[e] = static_cast<uint32_t>(a);
+            a += static_cast<uint64_t>(hthr[e]) + 1;
+            if (a > (uint64_t(1) << 32))
+                return fail(IMIN_ERR_INVALID, "LT weights: the in-edge shares of a vertex exceed 2^32");
+        }
+    }
 
     imin_graph* g = new imin_graph();
     cudaGetDevice(&g->device);
     g->dev = device_info();
     g->n = n;
     g->m = static_cast<int32_t>(m);
-    g->fingerprint = fingerprint(hrp, hcol, hthr, n, m, g->device);
+    g->model = model;
+    g->fingerprint = fingerprint(hrp, hcol, hthr, n, m, g->device) ^ (static_cast<uint64_t>(model) << 63);
     keep_pool_memory(g->device);
     const int64_t m4 = ((m + 3) / 4) * 4 + 4;  // padded so the last 16-byte group is in bounds
     hcol.resize(m4, 0);
@@ -1126,6 +1148,12 @@ int imin_load_graph(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t*
     cudaError_t e = cudaMalloc(&g->row_ptr, sizeof(int32_t) * (n + 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->col, sizeof(int32_t) * m4);
     if (e == cudaSuccess) e = cudaMalloc(&g->thr4, sizeof(uint32_t) * m4);
+    if (e == cudaSuccess && model == 1) {
+        hlo.resize(m4, 0);
+        e = cudaMalloc(&g->lo4, sizeof(uint32_t) * m4);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->lo4, hlo.data(), sizeof(uint32_t) * m4, cudaMemcpyHostToDevice, s);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->row_ptr, hrp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->col, hcol.data(), sizeof(int32_t) * m4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->thr4, hthr.data(), sizeof(uint32_t) * m4, cudaMemcpyHostToDevice, s);
@@ -1138,12 +1166,37 @@ int imin_load_graph(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t*
     return IMIN_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int imin_load_graph(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t* col,
+                    const uint32_t* thr, void* stream, imin_graph** out)
+{
+    g_err[0] = '\0';
+    return load_impl(n, m, row_ptr, col, thr, 0, stream, out);
+}
+
+int imin_load_graph_lt(int32_t n, int64_t m, const int32_t* row_ptr, const int32_t* col,
+                       const uint32_t* weight, void* stream, imin_graph** out)
+{
+    g_err[0] = '\0';
+    return load_impl(n, m, row_ptr, col, weight, 1, stream, out);
+}
+
+int imin_graph_model(const imin_graph* g)
+{
+    if (g == nullptr) return fail(IMIN_ERR_INVALID, "graph handle is NULL");
+    return g->model;
+}
+
 int imin_free_graph(imin_graph* g)
 {
     if (g == nullptr) return IMIN_OK;
     cudaFree(g->row_ptr);
     cudaFree(g->col);
     cudaFree(g->thr4);
+    cudaFree(g->lo4);
     delete g;
     return IMIN_OK;
 }

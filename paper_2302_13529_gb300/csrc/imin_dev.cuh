@@ -73,8 +73,50 @@ struct DevGraph {
     int32_t m;
     const int32_t* __restrict__ row_ptr;  // [n+1]
     const int32_t* __restrict__ col;      // [m], padded to a multiple of 4
-    const uint4* __restrict__ thr4;       // [ceil(m/4)] thresholds, 4 per vector
+    const uint4* __restrict__ thr4;       // [ceil(m/4)] IC: thresholds; LT: interval widths - 1
+    const uint4* __restrict__ lo4;        // LT: start of each in-edge's interval; nullptr for IC
 };
+
+// The 32-bit word of vertex v's triggering draw in sample j of call `round` (linear-threshold
+// model): word v & 3 of Philox4x32-10 at counter (v >> 2, j, round, 0x80000000). Edge words use
+// the last counter word e >> 34 = 0, so the two never share a counter.
+__device__ __forceinline__ uint32_t vertex_word(uint32_t v, uint32_t j, uint32_t round, uint32_t k0,
+                                                uint32_t k1)
+{
+    const uint4 r = philox4x32_10(make_uint4(v >> 2, j, round, 0x80000000u), k0, k1);
+    const uint32_t k = v & 3u;
+    return k == 0 ? r.x : (k == 1 ? r.y : (k == 2 ? r.z : r.w));
+}
+
+// Live mask (bit k: edge 4q + k) of the edges 4q .. 4q+3 that lie in [beg, end), in sample j of
+// call `round`; th = thr4[q].
+//   IC (Def. 4): edge e is live iff its Philox word (counter (q, j, round, 0), word e & 3) <= thr.
+//   LT (Sec. 4.5, linear-threshold triggering sets): edge e = (u, v) is live iff v's word lies in
+//   e's interval [lo, lo + thr], i.e. (word - lo) mod 2^32 <= thr; the in-edges of v hold disjoint
+//   intervals, so at most one of them is live.
+__device__ __forceinline__ uint32_t group_live(const DevGraph& g, uint32_t q, const uint4& th, int32_t beg,
+                                               int32_t end, uint32_t j, uint32_t round, uint32_t k0,
+                                               uint32_t k1)
+{
+    const int32_t e0 = static_cast<int32_t>(q << 2);
+    uint32_t in = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) in |= (e0 + k >= beg && e0 + k < end) ? (1u << k) : 0u;
+    if (g.lo4 == nullptr) {
+        const uint4 r = philox4x32_10(make_uint4(q, j, round, 0u), k0, k1);
+        const uint32_t m = (r.x <= th.x ? 1u : 0u) | (r.y <= th.y ? 2u : 0u) | (r.z <= th.z ? 4u : 0u) |
+                           (r.w <= th.w ? 8u : 0u);
+        return m & in;
+    }
+    const int4 c = __ldg(reinterpret_cast<const int4*>(g.col) + q);
+    const uint4 lo = __ldg(g.lo4 + q);
+    uint32_t m = 0;
+    if ((in & 1u) && vertex_word(static_cast<uint32_t>(c.x), j, round, k0, k1) - lo.x <= th.x) m |= 1u;
+    if ((in & 2u) && vertex_word(static_cast<uint32_t>(c.y), j, round, k0, k1) - lo.y <= th.y) m |= 2u;
+    if ((in & 4u) && vertex_word(static_cast<uint32_t>(c.z), j, round, k0, k1) - lo.z <= th.z) m |= 4u;
+    if ((in & 8u) && vertex_word(static_cast<uint32_t>(c.w), j, round, k0, k1) - lo.w <= th.w) m |= 8u;
+    return m;
+}
 
 // Control block of one Alg. 2 call (zeroed before it starts).
 struct RoundCtl {
@@ -329,12 +371,12 @@ __device__ __forceinline__ int run_sample(const SampleParams& P, const WarpSpace
                 if (t < total) {
                     const uint32_t q = (static_cast<uint32_t>(o_beg) >> 2) + (t - (o_incl - o_ng));
                     const uint4 th = __ldg(P.g.thr4 + q);
-                    const uint4 r = philox4x32_10(make_uint4(q, j, P.round, 0u), P.key_lo, P.key_hi);
+                    const uint32_t lm = group_live(P.g, q, th, o_beg, o_end, j, P.round, P.key_lo, P.key_hi);
                     const int32_t e0 = static_cast<int32_t>(q << 2);
-                    ok0 = (e0 + 0 >= o_beg) && (e0 + 0 < o_end) && (r.x <= th.x);
-                    ok1 = (e0 + 1 >= o_beg) && (e0 + 1 < o_end) && (r.y <= th.y);
-                    ok2 = (e0 + 2 >= o_beg) && (e0 + 2 < o_end) && (r.z <= th.z);
-                    ok3 = (e0 + 3 >= o_beg) && (e0 + 3 < o_end) && (r.w <= th.w);
+                    ok0 = (lm & 1u) != 0;
+                    ok1 = (lm & 2u) != 0;
+                    ok2 = (lm & 4u) != 0;
+                    ok3 = (lm & 8u) != 0;
                     if (ok0) { v0 = static_cast<uint32_t>(__ldg(P.g.col + e0 + 0)); ok0 = !excluded(P.excl, v0); }
                     if (ok1) { v1 = static_cast<uint32_t>(__ldg(P.g.col + e0 + 1)); ok1 = !excluded(P.excl, v1); }
                     if (ok2) { v2 = static_cast<uint32_t>(__ldg(P.g.col + e0 + 2)); ok2 = !excluded(P.excl, v2); }

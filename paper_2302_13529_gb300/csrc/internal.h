@@ -44,7 +44,9 @@ struct imin_graph {
     imin::DeviceInfo dev;
     int32_t* row_ptr = nullptr;  // [n+1]
     int32_t* col = nullptr;      // [m] padded to a multiple of 4 (+4)
-    uint4* thr4 = nullptr;       // thresholds, same padding
+    uint4* thr4 = nullptr;       // thresholds (LT: interval widths - 1), same padding
+    uint4* lo4 = nullptr;        // LT model: start of each in-edge's interval, same padding
+    int32_t model = 0;           // 0: independent cascade (Def. 4); 1: linear threshold (Sec. 4.5)
     // sampled hash of the CSR: handles of the same graph share tuning results
     uint64_t fingerprint = 0;
     // warp/block cutoff picked by the autotuner, per seed-set size class (ceil(log2 |S|));
@@ -55,6 +57,11 @@ struct imin_graph {
 };
 
 namespace imin {
+
+inline DevGraph dev_graph(const imin_graph* g)
+{
+    return DevGraph{g->n, g->m, g->row_ptr, g->col, g->thr4, g->lo4};
+}
 
 // Launch shape and capacities of the sample tiers for one graph / seed-set size.
 struct TierPlan {

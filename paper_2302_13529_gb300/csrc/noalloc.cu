@@ -239,7 +239,7 @@ extern "C" int imin_estimate_decrease_noalloc(const imin_graph* g, const int32_t
     if (hbad & 2u) return fail_msg(IMIN_ERR_INVALID, "seeds/blocked: duplicate vertex or blocked seed");
 
     SampleParams P{};
-    P.g = DevGraph{g->n, g->m, g->row_ptr, g->col, g->thr4};
+    P.g = dev_graph(g);
     P.seeds = dseeds;
     P.ns = static_cast<uint32_t>(n_seeds);
     P.excl = excl;

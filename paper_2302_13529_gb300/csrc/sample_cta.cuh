@@ -377,14 +377,7 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
                 const uint4 th = nth;
                 fetch(t0 + kCtaThreads + tid);
                 uint32_t m = 0;
-                if (oe > ob) {
-                    const uint4 r = philox4x32_10(make_uint4(q, j, P.round, 0u), P.key_lo, P.key_hi);
-                    const int32_t e0 = static_cast<int32_t>(q << 2);
-                    m |= (e0 + 0 >= ob && e0 + 0 < oe && r.x <= th.x) ? 1u : 0u;
-                    m |= (e0 + 1 >= ob && e0 + 1 < oe && r.y <= th.y) ? 2u : 0u;
-                    m |= (e0 + 2 >= ob && e0 + 2 < oe && r.z <= th.z) ? 4u : 0u;
-                    m |= (e0 + 3 >= ob && e0 + 3 < oe && r.w <= th.w) ? 8u : 0u;
-                }
+                if (oe > ob) m = group_live(P.g, q, th, ob, oe, j, P.round, P.key_lo, P.key_hi);
                 const uint32_t nc = __popc(m);
                 const uint32_t cincl = warp_incl_scan(nc, lane);
                 uint32_t w = staged + cincl - nc;

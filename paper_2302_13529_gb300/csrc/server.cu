@@ -146,7 +146,7 @@ namespace {
         }                                                                                \
     } while (0)
 
-DevGraph dev_graph_of(const imin_graph* g) { return DevGraph{g->n, g->m, g->row_ptr, g->col, g->thr4}; }
+DevGraph dev_graph_of(const imin_graph* g) { return dev_graph(g); }
 
 }  // namespace
 

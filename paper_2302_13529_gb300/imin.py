@@ -78,6 +78,8 @@ def lib():
         P = ctypes.c_void_p
         L.imin_load_graph.argtypes = [ctypes.c_int32, ctypes.c_int64, P, P, P, P,
                                       ctypes.POINTER(P)]
+        L.imin_load_graph_lt.argtypes = L.imin_load_graph.argtypes
+        L.imin_graph_model.argtypes = [P]
         L.imin_free_graph.argtypes = [P]
         L.imin_graph_info.argtypes = [P, P, P]
         L.imin_estimate_decrease.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int32,
@@ -141,21 +143,27 @@ def _ptr(a, dtype):
 
 
 class GraphHandle:
-    """A graph resident in device memory (imin_load_graph / imin_free_graph)."""
+    """A graph resident in device memory (imin_load_graph / imin_load_graph_lt / imin_free_graph).
+    model "ic": thr are independent-cascade thresholds; "lt": thr + 1 are the linear-threshold
+    shares of each vertex's in-edges."""
 
-    def __init__(self, n, row_ptr, col, thr, stream=None):
+    def __init__(self, n, row_ptr, col, thr, stream=None, model="ic"):
+        if model not in ("ic", "lt"):
+            raise ValueError(f"unknown model {model!r} (ic or lt)")
         rp, k1, _ = _ptr(row_ptr, np.int32)
         c, k2, m = _ptr(col, np.int32)
         t, k3, _ = _ptr(thr, np.uint32)
         h = ctypes.c_void_p()
-        _check(lib().imin_load_graph(int(n), int(m), rp, c, t, _stream(stream), ctypes.byref(h)))
+        load = lib().imin_load_graph if model == "ic" else lib().imin_load_graph_lt
+        _check(load(int(n), int(m), rp, c, t, _stream(stream), ctypes.byref(h)))
         self._h = h
         self.n = int(n)
         self.m = int(m)
+        self.model = model
 
     @classmethod
-    def from_graph(cls, g, stream=None):
-        return cls(g.n, g.row_ptr, g.col, g.thr, stream)
+    def from_graph(cls, g, stream=None, model="ic"):
+        return cls(g.n, g.row_ptr, g.col, g.thr, stream, model)
 
     @property
     def handle(self):
@@ -173,8 +181,8 @@ class GraphHandle:
             pass
 
 
-def load_graph(g, stream=None) -> GraphHandle:
-    return GraphHandle.from_graph(g, stream)
+def load_graph(g, stream=None, model="ic") -> GraphHandle:
+    return GraphHandle.from_graph(g, stream, model)
 
 
 def estimate_decrease(gh: GraphHandle, seeds, blocked, theta, key, round_=0, out=None,

@@ -17,10 +17,25 @@ def _stats(reached, examined, live, samples):
 
 
 def test_algorithmic_bytes_formula():
-    # 10 samples, 3 seeds each: 8|R| + 4 E_R + 4 L + 8 |R \ S|
+    # 10 samples, 3 seeds each: 8|R| + 8 E_R + 8 |R \ S|; with targets of live edges only:
+    # 8|R| + 4 E_R + 4 L + 8 |R \ S|
     st = _stats(reached=500, examined=7000, live=420, samples=10)
-    assert bench.algorithmic_bytes(st, 3, 3) == 8 * 500 + 4 * 7000 + 4 * 420 + 8 * (500 - 30)
+    assert bench.algorithmic_bytes(st, 3, 3) == 8 * 500 + 8 * 7000 + 8 * (500 - 30)
+    assert bench.algorithmic_bytes_live_targets(st, 3, 3) == 8 * 500 + 4 * 7000 + 4 * 420 + 8 * (500 - 30)
     assert bench.algorithmic_bytes(_stats(0, 0, 0, 0), 3, 50) == 0
+
+
+def test_roofline_names_its_bound():
+    """HBM when the kernel's DRAM traffic is of the order of its algorithmic bytes; instruction
+    issue when the graph is served from L2 (traffic far below them)."""
+    prof = {k: {"launches": 0, "ms": 0.0} for k in ("sample_tier0", "sample_tier1", "sample_tier2",
+                                                     "sample_cta", "select", "other")}
+    prof["sample_cta"] = {"launches": 2, "ms": 4.0}
+    st = _stats(reached=1000, examined=100000, live=900, samples=10)
+    r = bench.roofline_of(prof, st, 3, workload="no-such-workload")
+    assert r["kernel"] == "k_sample_cta" and r["bound"] == "hbm" and r["traffic"] is None
+    alg = (8 * 1000 + 8 * 100000 + 8 * (1000 - 30)) / 2
+    assert abs(r["achieved"] - alg / 2e-3 / 1e9) < 1e-9 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
 
 
 def test_traffic_only_for_the_sources_it_was_measured_on(tmp_path, monkeypatch):
@@ -70,6 +85,6 @@ def test_reference_arm_prints_the_contract_line():
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
     assert line["unit"] == "samples/s" and line["value"] > 0 and line["higher_is_better"] is True
     assert line["config"]["workload"] == bench.WORKLOAD
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
     assert line["e2e"] == {"value": line["value"], "unit": "samples/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
