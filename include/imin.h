@@ -144,6 +144,55 @@ int imin_greedy_replace(const imin_graph* g, const int32_t* seeds, int32_t n_see
                         uint32_t theta, uint64_t key, int32_t* out_blockers, int32_t* out_count,
                         void* stream);
 
+/* ---- comparison algorithms of the evaluation (Sec. 5) ------------------------------------
+ * The paper compares AdvancedGreedy and GreedyReplace with BaselineGreedy (Alg. 1, the earlier
+ * greedy that scores every candidate by Monte-Carlo simulation), Exact (every blocker set of
+ * size b scored by simulation), OutDegree and Rand. The simulated scores use the sampled graphs
+ * of the stream above: every set scored in one call sees the same samples (common random
+ * numbers), so a result depends only on its arguments. */
+
+/* Simulated spread (Def. 3) of many blocker sets at once:
+ *   out_sums[i] = sum over samples j in [0, theta) of call `round` of |R_j| (seeds included),
+ *   with `blocked` and the set_size vertices sets[i * set_size .. (i+1) * set_size - 1] blocked.
+ *   sets       int32[n_sets * set_size] (host or device): each set's vertices distinct, neither
+ *              seeds nor in `blocked`; 0 <= set_size <= 64
+ *   out_sums   uint64[n_sets] (host or device)
+ * Synchronizes `stream`. Errors: as imin_estimate_spread. */
+int imin_estimate_spread_sets(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
+                              const int32_t* blocked, int32_t n_blocked, const int32_t* sets,
+                              int32_t n_sets, int32_t set_size, uint32_t theta, uint64_t key,
+                              uint32_t round, uint64_t* out_sums, void* stream);
+
+/* BaselineGreedy (Alg. 1) with simulations of r sampled graphs: b rounds; in round i (0-based)
+ * every candidate u of V \ (S u B) is scored by its simulated spread decrease
+ * sum_j |R_j(B)| - |R_j(B u {u})| over samples j in [0, r) of call i, and the candidate with the
+ * largest decrease is appended (strict '>' in ascending id). Each round simulates r sampled
+ * graphs per candidate (O(n r m) work per round, as the paper states for Alg. 1). Stops early
+ * only when no candidate is left. Outputs as imin_advanced_greedy. Synchronizes `stream`. */
+int imin_baseline_greedy(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b,
+                         uint32_t r, uint64_t key, int32_t* out_blockers, int32_t* out_count,
+                         void* stream);
+
+/* Exact (Sec. 5, "Algorithms"): every k-subset of V \ S (k = min(b, n - n_seeds)) scored by its
+ * simulated spread over samples [0, r) of call 0; the first subset in lexicographic order with
+ * the smallest spread is returned in ascending ids (out_count = k). At most 10^8 subsets
+ * (IMIN_ERR_INVALID beyond). Synchronizes `stream`. */
+int imin_exact_blockers(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b,
+                        uint32_t r, uint64_t key, int32_t* out_blockers, int32_t* out_count,
+                        void* stream);
+
+/* OutDegree (Sec. 5): the min(b, n - n_seeds) non-seed vertices of largest out-degree, in that
+ * order (the smaller id first among equal degrees). out_blockers: host int32[b]. */
+int imin_out_degree_blockers(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b,
+                             int32_t* out_blockers, int32_t* out_count);
+
+/* Rand (Sec. 5): min(b, c) distinct non-seed vertices (c of them), by a partial Fisher-Yates
+ * shuffle of the non-seeds in ascending id: draw t swaps position t with position
+ * t + floor(w_t (c - t) / 2^32), w_t = word 0 of Philox4x32-10 at counter (t, 0, 0, 0xC0000000)
+ * under `key`. out_blockers: host int32[b]. */
+int imin_random_blockers(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b,
+                         uint64_t key, int32_t* out_blockers, int32_t* out_count);
+
 /* imin_estimate_decrease for callers that cannot allocate memory at call time (the paper has
  * no counterpart; this is a deployment variant).
  * Some callers must not allocate device memory when they call in: code whose device memory

@@ -732,6 +732,23 @@ static int reach_count(const graph_t *g, const int32_t *seeds, int32_t ns, uint6
     return 0;
 }
 
+/* *total += sum over samples j in [j0, j1) of |R_j| (seeds included), blocked vertices as marked
+ * in s: the sequential loop, or run_parallel. */
+static int spread_sum(const graph_t *g, const int32_t *seeds, int32_t ns, uint64_t key, uint32_t round,
+                      uint32_t j0, uint32_t j1, state_t *s, uint64_t *total)
+{
+    if (g_threads > 1 && j1 - j0 >= 2 * SAMPLE_BLOCK)
+        return run_parallel(g, seeds, ns, key, round, j0, j1, s, 1, NULL, total);
+    for (uint32_t j = j0; j < j1; j++) {
+        int64_t c = 0;
+        int rc = reach_count(g, seeds, ns, key, round, j, s, &c);
+        clear_sample(s);
+        if (rc) return rc;
+        *total += (uint64_t)c;
+    }
+    return 0;
+}
+
 /* *out_sum = sum over samples j in [j0, j1) of |R_j| (seeds included). */
 ORACLE_API int oracle_spread_range(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
                                    const uint32_t *thr, const int32_t *seeds, int32_t ns,
@@ -748,16 +765,7 @@ ORACLE_API int oracle_spread_range(int32_t n, int64_t m, const int32_t *row_ptr,
     }
     int rc = validate(&g, seeds, ns, blocked, nb, &s);
     uint64_t total = 0;
-    if (!rc && g_threads > 1 && j1 - j0 >= 2 * SAMPLE_BLOCK) {
-        rc = run_parallel(&g, seeds, ns, key, round, j0, j1, &s, 1, NULL, &total);
-    } else {
-        for (uint32_t j = j0; !rc && j < j1; j++) {
-            int64_t c = 0;
-            rc = reach_count(&g, seeds, ns, key, round, j, &s, &c);
-            total += (uint64_t)c;
-            clear_sample(&s);
-        }
-    }
+    if (!rc) rc = spread_sum(&g, seeds, ns, key, round, j0, j1, &s, &total);
     if (!rc) *out_sum = total;
     state_free(&s);
     free(lo);
@@ -904,5 +912,222 @@ ORACLE_API int oracle_greedy_replace(int32_t n, int64_t m, const int32_t *row_pt
     free(cand);
     state_free(&s);
     free(lo);
+    return rc;
+}
+
+
+/* ------------------------------------------------------------------------------------------
+ * The comparison algorithms of Sec. 5, all evaluated by simulation (Def. 3) on the sampled
+ * graphs of the same stream:
+ *   - spread of many blocker sets: every set sees the same samples j in [0, theta) of call
+ *     `round` (common random numbers);
+ *   - BaselineGreedy (Alg. 1): b rounds; in round i every candidate u of V \ (S u B) is scored
+ *     by its simulated spread decrease sum_j |R_j(B)| - |R_j(B u {u})| over samples j in
+ *     [0, r) of call i, and the largest decrease wins (strict '>' in ascending id);
+ *   - Exact: every min(b, |V \ S|)-subset of V \ S, in lexicographic order, scored by its
+ *     simulated spread over samples [0, r) of call 0; the first subset with the smallest spread
+ *     wins;
+ *   - OutDegree: the b non-seed vertices of largest out-degree (ties: smaller id first);
+ *   - Rand: b distinct non-seed vertices chosen uniformly by a partial Fisher-Yates shuffle of
+ *     the non-seeds in ascending id, draw t taking index t + floor(w_t * (c - t) / 2^32) with
+ *     w_t = word 0 of Philox4x32-10 at counter (t, 0, 0, 0xC0000000) under the key (c = number of
+ *     non-seeds).
+ * ---------------------------------------------------------------------------------------- */
+
+/* Simulated spread of blocked-set s: marks set members blocked, sums, unmarks. */
+static int spread_of_set(const graph_t *g, const int32_t *seeds, int32_t ns, const int32_t *set, int32_t k,
+                         uint64_t key, uint32_t round, uint32_t theta, state_t *s, uint64_t *out)
+{
+    int rc = 0;
+    int32_t marked = 0;
+    for (; marked < k; marked++) {
+        const int32_t v = set[marked];
+        if (v < 0 || v >= g->n || s->is_seed[v] || s->is_blocked[v]) {
+            rc = -1;
+            break;
+        }
+        s->is_blocked[v] = 1;
+    }
+    uint64_t total = 0;
+    if (!rc) rc = spread_sum(g, seeds, ns, key, round, 0, theta, s, &total);
+    for (int32_t i = 0; i < marked; i++) s->is_blocked[set[i]] = 0;
+    if (!rc) *out = total;
+    return rc;
+}
+
+ORACLE_API int oracle_spread_sets(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
+                                  const uint32_t *thr, const int32_t *seeds, int32_t ns,
+                                  const int32_t *blocked, int32_t nb, const int32_t *sets, int32_t nsets,
+                                  int32_t k, uint64_t key, uint32_t round, uint32_t theta,
+                                  uint64_t *out_sums, int32_t model)
+{
+    graph_t g = {n, m, row_ptr, col, thr, NULL};
+    uint32_t *lo = NULL;
+    if (nsets < 0 || k < 0 || graph_model(&g, model, &lo)) return -1;
+    state_t s;
+    if (state_init(&s, n)) {
+        free(lo);
+        return -1;
+    }
+    int rc = validate(&g, seeds, ns, blocked, nb, &s);
+    for (int32_t i = 0; i < nsets && !rc; i++)
+        rc = spread_of_set(&g, seeds, ns, sets + (int64_t)i * k, k, key, round, theta, &s, out_sums + i);
+    state_free(&s);
+    free(lo);
+    return rc;
+}
+
+ORACLE_API int oracle_baseline_greedy(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
+                                      const uint32_t *thr, const int32_t *seeds, int32_t ns, int32_t b,
+                                      uint32_t r, uint64_t key, int32_t *out_blockers, int32_t *out_count,
+                                      int32_t model)
+{
+    graph_t g = {n, m, row_ptr, col, thr, NULL};
+    uint32_t *lo = NULL;
+    if (b < 0 || r == 0 || graph_model(&g, model, &lo)) return -1;
+    state_t s;
+    if (state_init(&s, n)) {
+        free(lo);
+        return -1;
+    }
+    int rc = validate(&g, seeds, ns, NULL, 0, &s);
+    int32_t count = 0;
+    for (int32_t i = 0; i < b && !rc; i++) {
+        uint64_t base = 0;
+        rc = spread_sum(&g, seeds, ns, key, (uint32_t)i, 0, r, &s, &base);
+        int32_t x = -1;
+        uint64_t best = 0;
+        for (int32_t u = 0; u < n && !rc; u++) {
+            if (s.is_seed[u] || s.is_blocked[u]) continue;
+            uint64_t su = 0;
+            rc = spread_of_set(&g, seeds, ns, &u, 1, key, (uint32_t)i, r, &s, &su);
+            const uint64_t dec = base - su;  /* blocking u never adds reached vertices */
+            if (!rc && (x == -1 || dec > best)) {
+                x = u;
+                best = dec;
+            }
+        }
+        if (rc || x == -1) break;
+        out_blockers[count++] = x;
+        s.is_blocked[x] = 1;
+    }
+    *out_count = count;
+    state_free(&s);
+    free(lo);
+    return rc;
+}
+
+ORACLE_API int oracle_exact(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
+                            const uint32_t *thr, const int32_t *seeds, int32_t ns, int32_t b, uint32_t r,
+                            uint64_t key, int32_t *out_blockers, int32_t *out_count, int32_t model)
+{
+    graph_t g = {n, m, row_ptr, col, thr, NULL};
+    uint32_t *lo = NULL;
+    if (b < 0 || r == 0 || graph_model(&g, model, &lo)) return -1;
+    state_t s;
+    if (state_init(&s, n)) {
+        free(lo);
+        return -1;
+    }
+    int rc = validate(&g, seeds, ns, NULL, 0, &s);
+    int32_t *cand = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * ((size_t)b + 1));
+    int32_t *set = (int32_t *)malloc(sizeof(int32_t) * ((size_t)b + 1));
+    if (!cand || !idx || !set) rc = -1;
+    int32_t c = 0, k = 0;
+    if (!rc) {
+        for (int32_t u = 0; u < n; u++)
+            if (!s.is_seed[u]) cand[c++] = u;
+        k = b < c ? b : c;
+        for (int32_t i = 0; i < k; i++) idx[i] = i;
+        uint64_t best = 0;
+        int have = 0;
+        for (;;) {  /* k-subsets of cand in lexicographic order of their index vectors */
+            for (int32_t i = 0; i < k; i++) set[i] = cand[idx[i]];
+            uint64_t sp = 0;
+            rc = spread_of_set(&g, seeds, ns, set, k, key, 0, r, &s, &sp);
+            if (rc) break;
+            if (!have || sp < best) {
+                have = 1;
+                best = sp;
+                for (int32_t i = 0; i < k; i++) out_blockers[i] = set[i];
+            }
+            int32_t i = k - 1;
+            while (i >= 0 && idx[i] == c - k + i) i--;
+            if (i < 0) break;
+            idx[i]++;
+            for (int32_t t = i + 1; t < k; t++) idx[t] = idx[t - 1] + 1;
+        }
+    }
+    *out_count = rc ? 0 : k;
+    free(cand);
+    free(idx);
+    free(set);
+    state_free(&s);
+    free(lo);
+    return rc;
+}
+
+ORACLE_API int oracle_out_degree(int32_t n, const int32_t *row_ptr, const int32_t *seeds, int32_t ns,
+                                 int32_t b, int32_t *out_blockers, int32_t *out_count)
+{
+    if (n <= 0 || b < 0 || ns < 0) return -1;
+    uint8_t *taken = (uint8_t *)calloc((size_t)n, 1);
+    if (!taken) return -1;
+    for (int32_t i = 0; i < ns; i++) {
+        if (seeds[i] < 0 || seeds[i] >= n || taken[seeds[i]]) {
+            free(taken);
+            return -1;
+        }
+        taken[seeds[i]] = 1;
+    }
+    int32_t count = 0;
+    for (; count < b; count++) {  /* b selection passes: the largest remaining out-degree */
+        int32_t x = -1;
+        for (int32_t u = 0; u < n; u++)
+            if (!taken[u] && (x == -1 || row_ptr[u + 1] - row_ptr[u] > row_ptr[x + 1] - row_ptr[x])) x = u;
+        if (x == -1) break;
+        out_blockers[count] = x;
+        taken[x] = 1;
+    }
+    *out_count = count;
+    free(taken);
+    return 0;
+}
+
+ORACLE_API int oracle_random_blockers(int32_t n, const int32_t *seeds, int32_t ns, int32_t b, uint64_t key,
+                                      int32_t *out_blockers, int32_t *out_count)
+{
+    if (n <= 0 || b < 0 || ns < 0) return -1;
+    uint8_t *is_seed = (uint8_t *)calloc((size_t)n, 1);
+    int32_t *cand = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!is_seed || !cand) {
+        free(is_seed);
+        free(cand);
+        return -1;
+    }
+    int rc = 0;
+    for (int32_t i = 0; i < ns && !rc; i++) {
+        if (seeds[i] < 0 || seeds[i] >= n || is_seed[seeds[i]]) rc = -1;
+        else is_seed[seeds[i]] = 1;
+    }
+    int32_t c = 0;
+    for (int32_t u = 0; u < n && !rc; u++)
+        if (!is_seed[u]) cand[c++] = u;
+    const int32_t k = rc ? 0 : (b < c ? b : c);
+    const uint32_t kk[2] = {(uint32_t)key, (uint32_t)(key >> 32)};
+    for (int32_t t = 0; t < k; t++) {
+        const uint32_t ctr[4] = {(uint32_t)t, 0, 0, 0xC0000000u};
+        uint32_t w[4];
+        oracle_philox4x32_10(ctr, kk, w);
+        const int32_t pick = t + (int32_t)(((uint64_t)w[0] * (uint64_t)(c - t)) >> 32);
+        const int32_t tmp = cand[t];
+        cand[t] = cand[pick];
+        cand[pick] = tmp;
+        out_blockers[t] = cand[t];
+    }
+    *out_count = k;
+    free(is_seed);
+    free(cand);
     return rc;
 }

@@ -79,8 +79,20 @@ def lib():
             L.oracle_set_threads.restype = None
             L.oracle_get_threads.restype = ctypes.c_int32
             L.oracle_last_calls.restype = ctypes.c_int32
+            L.oracle_spread_sets.argtypes = g + [_i32p, ctypes.c_int32, _i32p, ctypes.c_int32, _i32p,
+                                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                                 ctypes.c_uint32, ctypes.c_uint32, _u64p]
+            for name in ("oracle_baseline_greedy", "oracle_exact"):
+                getattr(L, name).argtypes = g + [_i32p, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_uint32, ctypes.c_uint64, _i32p,
+                                                 ctypes.POINTER(ctypes.c_int32)]
+            L.oracle_out_degree.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32, ctypes.c_int32,
+                                            _i32p, ctypes.POINTER(ctypes.c_int32)]
+            L.oracle_random_blockers.argtypes = [ctypes.c_int32, _i32p, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_uint64, _i32p, ctypes.POINTER(ctypes.c_int32)]
             for name in ("oracle_sample", "oracle_decrease_range", "oracle_decrease",
-                         "oracle_advanced_greedy", "oracle_greedy_replace", "oracle_spread_range"):
+                         "oracle_advanced_greedy", "oracle_greedy_replace", "oracle_spread_range",
+                         "oracle_spread_sets", "oracle_baseline_greedy", "oracle_exact"):
                 f = getattr(L, name)
                 f.argtypes = f.argtypes + [ctypes.c_int32]  # model: 0 = IC, 1 = LT
                 f.restype = ctypes.c_int
@@ -223,4 +235,66 @@ def greedy_replace(graph, seeds, b, theta, key, model="ic") -> np.ndarray:
     cnt = ctypes.c_int32()
     _check(lib().oracle_greedy_replace(n, m, rp, col, thr, s, ns, b, theta, key, out,
                                        ctypes.byref(cnt), _model(model)), "greedy_replace")
+    return out[:cnt.value].copy()
+
+
+# --------------------------------------------------------------------------------------------
+# comparison algorithms of Sec. 5 (evaluated by simulation on the same sampled graphs)
+# --------------------------------------------------------------------------------------------
+
+def spread_sets(graph, seeds, blocked, sets, theta, key, round_=0, model="ic") -> np.ndarray:
+    """uint64[len(sets)]: for each blocker set (a row of `sets`, added to `blocked`), the sum of
+    |R| over samples [0, theta) of call `round_` (common random numbers for all sets)."""
+    n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
+    s, ns = _ids(seeds)
+    b, nb = _ids(blocked)
+    arr = np.ascontiguousarray(np.asarray(sets, dtype=np.int32).reshape(len(sets), -1))
+    k = int(arr.shape[1]) if len(sets) else 0
+    flat = arr.reshape(-1) if arr.size else np.zeros(1, np.int32)
+    out = np.zeros(max(len(sets), 1), dtype=np.uint64)
+    _check(lib().oracle_spread_sets(n, m, rp, col, thr, s, ns, b, nb, flat, len(sets), k, key, round_,
+                                    theta, out, _model(model)), "spread_sets")
+    return out[:len(sets)]
+
+
+def baseline_greedy(graph, seeds, b, r, key, model="ic") -> np.ndarray:
+    """Alg. 1 BaselineGreedy with r-sample simulations per candidate (round i: samples [0, r) of
+    call i for every candidate)."""
+    n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
+    s, ns = _ids(seeds)
+    out = np.zeros(max(b, 1), dtype=np.int32)
+    cnt = ctypes.c_int32()
+    _check(lib().oracle_baseline_greedy(n, m, rp, col, thr, s, ns, b, r, key, out, ctypes.byref(cnt),
+                                        _model(model)), "baseline_greedy")
+    return out[:cnt.value].copy()
+
+
+def exact(graph, seeds, b, r, key, model="ic") -> np.ndarray:
+    """Exact: the min(b, |V \\ S|)-subset of V \\ S with the smallest simulated spread over samples
+    [0, r) of call 0 (the first in lexicographic order among ties), ascending ids."""
+    n, m, rp, col, thr = _g(graph.n, graph.row_ptr, graph.col, graph.thr)
+    s, ns = _ids(seeds)
+    out = np.zeros(max(b, 1), dtype=np.int32)
+    cnt = ctypes.c_int32()
+    _check(lib().oracle_exact(n, m, rp, col, thr, s, ns, b, r, key, out, ctypes.byref(cnt), _model(model)),
+           "exact")
+    return out[:cnt.value].copy()
+
+
+def out_degree_blockers(graph, seeds, b) -> np.ndarray:
+    """OutDegree: the b non-seeds of largest out-degree, in that order (smaller id first on ties)."""
+    s, ns = _ids(seeds)
+    out = np.zeros(max(b, 1), dtype=np.int32)
+    cnt = ctypes.c_int32()
+    _check(lib().oracle_out_degree(int(graph.n), np.ascontiguousarray(graph.row_ptr, dtype=np.int32), s, ns,
+                                   b, out, ctypes.byref(cnt)), "out_degree")
+    return out[:cnt.value].copy()
+
+
+def random_blockers(n, seeds, b, key) -> np.ndarray:
+    """Rand: b distinct non-seeds by a Philox-driven partial Fisher-Yates shuffle."""
+    s, ns = _ids(seeds)
+    out = np.zeros(max(b, 1), dtype=np.int32)
+    cnt = ctypes.c_int32()
+    _check(lib().oracle_random_blockers(int(n), s, ns, b, key, out, ctypes.byref(cnt)), "random_blockers")
     return out[:cnt.value].copy()

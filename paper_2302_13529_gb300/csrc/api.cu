@@ -364,6 +364,8 @@ SampleParams sample_params(const imin_graph* g, const Query& q, uint32_t ns, uin
     P.lists = q.lists;
     P.done = done;
     P.stats = q.stats;
+    P.extra = nullptr;
+    P.n_extra = 0;
     return P;
 }
 
@@ -566,6 +568,20 @@ int cutoff_for(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t 
     return IMIN_OK;
 }
 
+}  // namespace
+
+namespace imin {
+
+int tuned_cutoff(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t key, uint32_t theta_hint,
+                 cudaStream_t s, uint32_t* out)
+{
+    return cutoff_for(g, seeds, key, theta_hint, s, out);
+}
+
+}  // namespace imin
+
+namespace {
+
 int estimate_impl(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
                   const int32_t* blocked, int32_t n_blocked, uint32_t theta, uint64_t key,
                   uint32_t round, uint64_t* out_delta, imin_stats* stats, void* stream)
@@ -677,6 +693,101 @@ int spread_impl(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, cons
     record_stats(hstats);
     *out_sum = hsum;
     return IMIN_OK;
+}
+
+// ---- comparison algorithms of Sec. 5 (scored by simulation) --------------------------------
+
+// Simulated spread of `nsets` blocker sets of k vertices each (host array hsets), on top of the
+// blocked vertices hblocked: hsums[i] = sum over samples [0, theta) of call `round` of |R| with
+// set i blocked. mark: 1 for seeds, 2 for hblocked, 0 otherwise (restored on return).
+int spread_sets_core(const imin_graph* g, const std::vector<int32_t>& hseeds, const std::vector<int32_t>& hblocked,
+                     std::vector<uint8_t>& mark, const int32_t* hsets, int64_t nsets, int32_t k, uint32_t theta,
+                     uint64_t key, uint32_t round, uint64_t* hsums, cudaStream_t s)
+{
+    if (nsets < 0 || k < 0 || k > 64) return fail(IMIN_ERR_INVALID, "sets: need n_sets >= 0 and 0 <= set_size <= 64");
+    if (nsets == 0) return IMIN_OK;
+    if (static_cast<double>(nsets) * theta > 9.0e18) return fail(IMIN_ERR_INVALID, "n_sets * theta too large");
+    for (int64_t i = 0; i < nsets; ++i) {
+        const int32_t* set = hsets + i * k;
+        int rc = IMIN_OK;
+        int32_t j = 0;
+        for (; j < k; ++j) {
+            const int32_t v = set[j];
+            if (v < 0 || v >= g->n) { rc = fail(IMIN_ERR_INVALID, "sets: vertex id out of range"); break; }
+            if (mark[v] != 0) {
+                rc = fail(IMIN_ERR_INVALID, "sets: a vertex is a seed, blocked, or repeated in its set");
+                break;
+            }
+            mark[v] = 3;
+        }
+        for (int32_t t = 0; t < j; ++t) mark[set[t]] = 0;
+        if (rc) return rc;
+    }
+    Query q(s);
+    int rc = setup_query(g, hseeds, theta, nullptr, 0, q);
+    if (rc) return rc;
+    if (!q.plan.use_cta) return fail(IMIN_ERR_INTERNAL, "the spread kernel needs the block-per-sample tier");
+    RoundCtl* ctl = nullptr;
+    int32_t* dblocked = nullptr;
+    int32_t* dsets = nullptr;
+    unsigned long long* dsums = nullptr;
+    unsigned long long* cursor = nullptr;
+    IMIN_CUDA(q.arena.alloc(&ctl, 1));
+    IMIN_CUDA(q.arena.alloc(&dblocked, hblocked.size()));
+    IMIN_CUDA(q.arena.alloc(&dsets, static_cast<uint64_t>(nsets) * k));
+    IMIN_CUDA(q.arena.alloc(&dsums, static_cast<uint64_t>(nsets)));
+    IMIN_CUDA(q.arena.alloc(&cursor, 1));
+    IMIN_CUDA(cudaMemsetAsync(ctl, 0, sizeof(RoundCtl), s));
+    IMIN_CUDA(cudaMemsetAsync(dsums, 0, sizeof(unsigned long long) * nsets, s));
+    IMIN_CUDA(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s));
+    if (k > 0)
+        IMIN_CUDA(cudaMemcpyAsync(dsets, hsets, sizeof(int32_t) * nsets * k, cudaMemcpyHostToDevice, s));
+    if (!hblocked.empty()) {
+        IMIN_CUDA(cudaMemcpyAsync(dblocked, hblocked.data(), sizeof(int32_t) * hblocked.size(),
+                                  cudaMemcpyHostToDevice, s));
+        IMIN_CUDA(launch_build_excl(q.excl, dblocked, static_cast<int32_t>(hblocked.size()), s));
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    CallTimer T(s);
+    const SampleParams P = sample_params(g, q, static_cast<uint32_t>(hseeds.size()), theta, key, round, ctl, nullptr);
+    IMIN_CUDA(T.run(kKindCta, [&](bool* launched) {
+        *launched = true;
+        return launch_spread_sets(P, q.plan.cta, q.plan.blocks[kTierCta], q.plan.smem_bytes[kTierCta], q.scratch3,
+                                  dsets, static_cast<uint32_t>(k),
+                                  static_cast<unsigned long long>(nsets) * theta, cursor, dsums, s);
+    }));
+    RoundCtl hctl;
+    IMIN_CUDA(cudaMemcpyAsync(&hctl, ctl, sizeof(hctl), cudaMemcpyDeviceToHost, s));
+    IMIN_CUDA(cudaMemcpyAsync(hsums, dsums, sizeof(uint64_t) * nsets, cudaMemcpyDeviceToHost, s));
+    IMIN_CUDA(cudaStreamSynchronize(s));
+    T.collect();
+    if (hctl.error & kErrCapacity)
+        return fail(IMIN_ERR_CAPACITY, "a sampled cascade exceeded the block tier's slot capacity (2^18 vertices)");
+    if (hctl.error & kErrInternal) return fail(IMIN_ERR_INTERNAL, "the spread kernel failed");
+    return IMIN_OK;
+}
+
+// Philox4x32-10 on the host (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 3.3), for the random
+// blocker baseline.
+void philox_host(const uint32_t ctr[4], uint64_t key, uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = static_cast<uint32_t>(key), k1 = static_cast<uint32_t>(key >> 32);
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = 0xD2511F53ull * x0, p1 = 0xCD9E8D57ull * x2;
+        const uint32_t y0 = static_cast<uint32_t>(p1 >> 32) ^ x1 ^ k0;
+        const uint32_t y2 = static_cast<uint32_t>(p0 >> 32) ^ x3 ^ k1;
+        x1 = static_cast<uint32_t>(p1);
+        x3 = static_cast<uint32_t>(p0);
+        x0 = y0;
+        x2 = y2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = x0;
+    out[1] = x1;
+    out[2] = x2;
+    out[3] = x3;
 }
 
 enum class Driver { kAdvancedGreedy, kGreedyReplace };
@@ -870,14 +981,22 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         else cta_bytes = std::max(cta_bytes, bytes);
     }
     const TierPlan wp = plan_tiers(g0->dev, max_n, max_m, max_ns, 0);
-    // the warp tier in front: queries whose seed sets fit its shared-memory working set
+    bool all_ic = true;  // every graph IC: the launches take the IC-only kernels
+    for (int32_t i = 0; i < nq; ++i) all_ic = all_ic && qs[i].graph->model == 0;
+    // the warp tier in front: queries whose seed sets fit its shared-memory working set and whose
+    // graph's tuned warp/block cutoff (the single-query autotuner's, per graph and seed-set size
+    // class, tuned here on first use) is not 0; the launch holds the largest of those cutoffs
     std::vector<uint8_t> warp_q(nq, 0);
-    uint32_t warp_ns = 0;
-    const uint32_t cutoff = batch_cutoff();
+    uint32_t warp_ns = 0, cutoff = 0;
     for (int32_t i = 0; i < nq; ++i) {
-        if (cutoff > 0 && static_cast<uint32_t>(qs[i].n_seeds) <= kBatchWarpMaxSeeds) {
+        if (static_cast<uint32_t>(qs[i].n_seeds) > kBatchWarpMaxSeeds) continue;
+        uint32_t c = 0;
+        const int rc = tuned_cutoff(qs[i].graph, hseeds[i], qs[i].key, qs[i].theta, s, &c);
+        if (rc) return rc;
+        if (c > 0) {
             warp_q[i] = 1;
             warp_ns = std::max<uint32_t>(warp_ns, static_cast<uint32_t>(qs[i].n_seeds));
+            cutoff = std::max(cutoff, c);
         }
     }
     TierCfg wcfg{};
@@ -1024,6 +1143,7 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         B.over = over;
         B.over_cap = static_cast<uint32_t>(std::min<uint64_t>(sum_theta, 0xFFFFFFFFull));
         B.stats = stats;
+        B.all_ic = all_ic ? 1u : 0u;
         if (gr) {  // phase-2 unblocking of every GreedyReplace query at this step
             IMIN_CUDA(T.run(kKindOther, [&](bool* l) { *l = true; return launch_batch_unblock(B, rs); }));
         }
@@ -1320,6 +1440,200 @@ int imin_greedy_replace(const imin_graph* g, const int32_t* seeds, int32_t n_see
     g_err[0] = '\0';
     return greedy_impl(Driver::kGreedyReplace, g, seeds, n_seeds, b, theta, key, out_blockers,
                        out_count, stream);
+}
+
+int imin_estimate_spread_sets(const imin_graph* g, const int32_t* seeds, int32_t n_seeds,
+                              const int32_t* blocked, int32_t n_blocked, const int32_t* sets,
+                              int32_t n_sets, int32_t set_size, uint32_t theta, uint64_t key,
+                              uint32_t round, uint64_t* out_sums, void* stream)
+{
+    g_err[0] = '\0';
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int32_t> hseeds, hblocked, hsets;
+    std::vector<uint8_t> mark;
+    int rc = common_checks(g, seeds, n_seeds, theta, s, hseeds, mark);
+    if (rc) return rc;
+    if (n_blocked < 0 || n_sets < 0 || set_size < 0)
+        return fail(IMIN_ERR_INVALID, "n_blocked, n_sets and set_size must be >= 0");
+    if (n_sets > 0 && out_sums == nullptr) return fail(IMIN_ERR_INVALID, "out_sums is NULL");
+    rc = to_host(blocked, n_blocked, hblocked, s, "blocked");
+    if (!rc) rc = check_ids(hblocked, g->n, mark, 2, "blocked");
+    if (!rc) rc = to_host(sets, static_cast<int64_t>(n_sets) * set_size, hsets, s, "sets");
+    if (rc) return rc;
+    std::vector<uint64_t> hsums(static_cast<size_t>(n_sets));
+    rc = spread_sets_core(g, hseeds, hblocked, mark, hsets.data(), n_sets, set_size, theta, key, round,
+                          hsums.data(), s);
+    if (rc || n_sets == 0) return rc;
+    if (is_device_ptr(out_sums)) {
+        IMIN_CUDA(cudaMemcpyAsync(out_sums, hsums.data(), sizeof(uint64_t) * n_sets, cudaMemcpyHostToDevice, s));
+        IMIN_CUDA(cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(out_sums, hsums.data(), sizeof(uint64_t) * n_sets);
+    }
+    return IMIN_OK;
+}
+
+int imin_baseline_greedy(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b, uint32_t r,
+                         uint64_t key, int32_t* out_blockers, int32_t* out_count, void* stream)
+{
+    g_err[0] = '\0';
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int32_t> hseeds;
+    std::vector<uint8_t> mark;
+    int rc = common_checks(g, seeds, n_seeds, r, s, hseeds, mark);
+    if (rc) return rc;
+    if (b < 0) return fail(IMIN_ERR_INVALID, "b must be >= 0");
+    if (out_count == nullptr) return fail(IMIN_ERR_INVALID, "out_count is NULL");
+    if (b > 0 && out_blockers == nullptr) return fail(IMIN_ERR_INVALID, "out_blockers is NULL");
+    *out_count = 0;
+    std::vector<int32_t> B, cand;
+    std::vector<uint64_t> sums;
+    for (int32_t i = 0; i < b; ++i) {
+        cand.clear();
+        for (int32_t u = 0; u < g->n; ++u)
+            if (mark[u] == 0) cand.push_back(u);
+        if (cand.empty()) break;
+        sums.resize(cand.size());
+        // the common spread of G[V \ B] cancels in the decrease: the largest decrease is the
+        // smallest spread with u blocked (strict '<' in ascending id keeps the smallest id)
+        rc = spread_sets_core(g, hseeds, B, mark, cand.data(), static_cast<int64_t>(cand.size()), 1, r, key,
+                              static_cast<uint32_t>(i), sums.data(), s);
+        if (rc) return rc;
+        size_t x = 0;
+        for (size_t t = 1; t < cand.size(); ++t)
+            if (sums[t] < sums[x]) x = t;
+        B.push_back(cand[x]);
+        mark[cand[x]] = 2;
+    }
+    if (!B.empty()) {
+        if (is_device_ptr(out_blockers)) {
+            IMIN_CUDA(cudaMemcpyAsync(out_blockers, B.data(), 4 * B.size(), cudaMemcpyHostToDevice, s));
+            IMIN_CUDA(cudaStreamSynchronize(s));
+        } else {
+            std::memcpy(out_blockers, B.data(), 4 * B.size());
+        }
+    }
+    *out_count = static_cast<int32_t>(B.size());
+    return IMIN_OK;
+}
+
+int imin_exact_blockers(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b, uint32_t r,
+                        uint64_t key, int32_t* out_blockers, int32_t* out_count, void* stream)
+{
+    g_err[0] = '\0';
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int32_t> hseeds;
+    std::vector<uint8_t> mark;
+    int rc = common_checks(g, seeds, n_seeds, r, s, hseeds, mark);
+    if (rc) return rc;
+    if (b < 0) return fail(IMIN_ERR_INVALID, "b must be >= 0");
+    if (out_count == nullptr) return fail(IMIN_ERR_INVALID, "out_count is NULL");
+    if (b > 0 && out_blockers == nullptr) return fail(IMIN_ERR_INVALID, "out_blockers is NULL");
+    *out_count = 0;
+    std::vector<int32_t> cand;
+    for (int32_t u = 0; u < g->n; ++u)
+        if (mark[u] == 0) cand.push_back(u);
+    const int32_t c = static_cast<int32_t>(cand.size());
+    const int32_t k = std::min(b, c);
+    if (k > 64) return fail(IMIN_ERR_INVALID, "exact: at most 64 blockers");
+    double subsets = 1.0;  // C(c, k)
+    for (int32_t i = 0; i < k; ++i) subsets = subsets * (c - i) / (i + 1);
+    if (subsets > 1.0e8) return fail(IMIN_ERR_INVALID, "exact: more than 10^8 blocker sets to score");
+    constexpr int64_t kChunk = 1 << 16;
+    std::vector<int32_t> idx(static_cast<size_t>(k)), sets, best_set;
+    std::vector<uint64_t> sums;
+    for (int32_t i = 0; i < k; ++i) idx[i] = i;
+    uint64_t best = 0;
+    bool have = false, more = true;
+    const std::vector<int32_t> none;
+    while (more) {
+        // the next chunk of k-subsets in lexicographic order of their index vectors
+        sets.clear();
+        int64_t count = 0;
+        while (more && count < kChunk) {
+            for (int32_t i = 0; i < k; ++i) sets.push_back(cand[idx[i]]);
+            ++count;
+            int32_t i = k - 1;
+            while (i >= 0 && idx[i] == c - k + i) --i;
+            if (i < 0) {
+                more = false;
+            } else {
+                ++idx[i];
+                for (int32_t t = i + 1; t < k; ++t) idx[t] = idx[t - 1] + 1;
+            }
+        }
+        sums.resize(static_cast<size_t>(count));
+        rc = spread_sets_core(g, hseeds, none, mark, sets.data(), count, k, r, key, 0, sums.data(), s);
+        if (rc) return rc;
+        for (int64_t t = 0; t < count; ++t) {
+            if (!have || sums[t] < best) {
+                have = true;
+                best = sums[t];
+                best_set.assign(sets.begin() + t * k, sets.begin() + (t + 1) * k);
+            }
+        }
+    }
+    if (k > 0) {
+        if (is_device_ptr(out_blockers)) {
+            IMIN_CUDA(cudaMemcpyAsync(out_blockers, best_set.data(), 4ull * k, cudaMemcpyHostToDevice, s));
+            IMIN_CUDA(cudaStreamSynchronize(s));
+        } else {
+            std::memcpy(out_blockers, best_set.data(), 4ull * k);
+        }
+    }
+    *out_count = k;
+    return IMIN_OK;
+}
+
+int imin_out_degree_blockers(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b,
+                             int32_t* out_blockers, int32_t* out_count)
+{
+    g_err[0] = '\0';
+    std::vector<int32_t> hseeds;
+    std::vector<uint8_t> mark;
+    int rc = common_checks(g, seeds, n_seeds, 1, nullptr, hseeds, mark);
+    if (rc) return rc;
+    if (b < 0 || out_count == nullptr || (b > 0 && out_blockers == nullptr))
+        return fail(IMIN_ERR_INVALID, "b must be >= 0 and the outputs non-NULL");
+    std::vector<int32_t> rp(static_cast<size_t>(g->n) + 1);
+    IMIN_CUDA(cudaMemcpy(rp.data(), g->row_ptr, sizeof(int32_t) * (g->n + 1), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> cand;
+    for (int32_t u = 0; u < g->n; ++u)
+        if (mark[u] == 0) cand.push_back(u);
+    std::stable_sort(cand.begin(), cand.end(), [&](int32_t a, int32_t c) {
+        return rp[a + 1] - rp[a] > rp[c + 1] - rp[c];
+    });
+    const int32_t k = std::min<int32_t>(b, static_cast<int32_t>(cand.size()));
+    for (int32_t i = 0; i < k; ++i) out_blockers[i] = cand[i];
+    *out_count = k;
+    return IMIN_OK;
+}
+
+int imin_random_blockers(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, int32_t b, uint64_t key,
+                         int32_t* out_blockers, int32_t* out_count)
+{
+    g_err[0] = '\0';
+    std::vector<int32_t> hseeds;
+    std::vector<uint8_t> mark;
+    int rc = common_checks(g, seeds, n_seeds, 1, nullptr, hseeds, mark);
+    if (rc) return rc;
+    if (b < 0 || out_count == nullptr || (b > 0 && out_blockers == nullptr))
+        return fail(IMIN_ERR_INVALID, "b must be >= 0 and the outputs non-NULL");
+    std::vector<int32_t> cand;
+    for (int32_t u = 0; u < g->n; ++u)
+        if (mark[u] == 0) cand.push_back(u);
+    const int32_t c = static_cast<int32_t>(cand.size());
+    const int32_t k = std::min(b, c);
+    for (int32_t t = 0; t < k; ++t) {
+        const uint32_t ctr[4] = {static_cast<uint32_t>(t), 0u, 0u, 0xC0000000u};
+        uint32_t w[4];
+        philox_host(ctr, key, w);
+        const int32_t pick = t + static_cast<int32_t>((static_cast<uint64_t>(w[0]) * static_cast<uint64_t>(c - t)) >> 32);
+        std::swap(cand[t], cand[pick]);
+        out_blockers[t] = cand[t];
+    }
+    *out_count = k;
+    return IMIN_OK;
 }
 
 }  // extern "C"

@@ -79,7 +79,7 @@ __device__ __forceinline__ SampleParams params_of(const BatchQuery& Q, uint32_t 
     return P;
 }
 
-template <bool kSmemBitmap>
+template <bool kSmemBitmap, int M>
 __global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCfg C)
 {
     extern __shared__ __align__(16) uint32_t dsm[];
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCf
         const unsigned long long j1 = min(j0 + B.chunk, static_cast<unsigned long long>(Q.theta));
         for (unsigned long long j = j0; j < j1; ++j) {
             if (Q.done != nullptr && Q.done[j] != 0) continue;  // the warp tier finished it
-            const int rc = run_sample_cta<kSmemBitmap>(P, C, bm, dsm, sh, S, static_cast<uint32_t>(j), tid,
+            const int rc = run_sample_cta<kSmemBitmap, false, M>(P, C, bm, dsm, sh, S, static_cast<uint32_t>(j), tid,
                                                        sc, examined, live);
             if (tid == 0) {
                 if (rc == kSampleOverflow) {
@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCf
 // The warp tier of a step: one warp per sample, working set in shared memory with the
 // warp/block cutoff as capacity, over the active queries that have a `done` array. Each
 // sample's outcome is stored in done[j] (1: counted here; 0: left to the block tier).
+template <int M>
 __global__ void __launch_bounds__(kBatchWarps * 32, 4) k_batch_warp(BatchStep B, TierCfg T)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4) k_batch_warp(BatchStep B,
         const unsigned long long j0 = (item - B.prefix[q]) * B.chunk;
         const unsigned long long j1 = min(j0 + B.chunk, static_cast<unsigned long long>(Q.theta));
         for (unsigned long long j = j0; j < j1; ++j) {
-            const int rc = run_sample<false, true>(P, w, static_cast<uint32_t>(j), lane, sc);
+            const int rc = run_sample<false, true, M>(P, w, static_cast<uint32_t>(j), lane, sc);
             if (lane == 0) {
                 Q.done[j] = rc == kSampleDone ? 1 : 0;
                 if (rc == kSampleError) atomicOr(&B.ctl->error, kErrInternal);
@@ -324,11 +325,15 @@ bool plan_batch_cta(const DeviceInfo& dev, int32_t max_n, int32_t max_m, CtaCfg*
     if (!plan_cta_tier(dev, max_n, max_m, c, &b0, smem, &s0)) return false;
     int occ = 0;
     if (c->global_bitmap) {
-        if (allow_max_dynamic_smem(k_batch_cta<false>, dev) != cudaSuccess) return false;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta<false>, kCtaThreads, *smem);
+        if (allow_max_dynamic_smem(k_batch_cta<false, kModelIC>, dev) != cudaSuccess ||
+            allow_max_dynamic_smem(k_batch_cta<false, kModelAny>, dev) != cudaSuccess)
+            return false;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta<false, kModelIC>, kCtaThreads, *smem);
     } else {
-        if (allow_max_dynamic_smem(k_batch_cta<true>, dev) != cudaSuccess) return false;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta<true>, kCtaThreads, *smem);
+        if (allow_max_dynamic_smem(k_batch_cta<true, kModelIC>, dev) != cudaSuccess ||
+            allow_max_dynamic_smem(k_batch_cta<true, kModelAny>, dev) != cudaSuccess)
+            return false;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta<true, kModelIC>, kCtaThreads, *smem);
     }
     if (occ <= 0) return false;
     *blocks = static_cast<uint32_t>(occ) * dev.sms;
@@ -343,9 +348,11 @@ bool plan_batch_warp(const DeviceInfo& dev, uint32_t max_ns, uint32_t cutoff, Ti
     tier0_cfg(max_ns, cutoff, c);
     *smem = kBatchWarps * (kWarpStageBytes + c->warp_bytes);
     if (*smem > dev.smem_optin) return false;
-    if (allow_max_dynamic_smem(k_batch_warp, dev) != cudaSuccess) return false;
+    if (allow_max_dynamic_smem(k_batch_warp<kModelIC>, dev) != cudaSuccess ||
+        allow_max_dynamic_smem(k_batch_warp<kModelAny>, dev) != cudaSuccess)
+        return false;
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_warp, kBatchWarps * 32, *smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_warp<kModelIC>, kBatchWarps * 32, *smem);
     if (occ <= 0) return false;
     *blocks = static_cast<uint32_t>(occ) * dev.sms;
     return true;
@@ -354,15 +361,9 @@ bool plan_batch_warp(const DeviceInfo& dev, uint32_t max_ns, uint32_t cutoff, Ti
 cudaError_t launch_batch_warp(const BatchStep& B, const TierCfg& c, uint32_t blocks, uint64_t smem,
                               cudaStream_t s)
 {
-    k_batch_warp<<<blocks, kBatchWarps * 32, smem, s>>>(B, c);
+    if (B.all_ic) k_batch_warp<kModelIC><<<blocks, kBatchWarps * 32, smem, s>>>(B, c);
+    else k_batch_warp<kModelAny><<<blocks, kBatchWarps * 32, smem, s>>>(B, c);
     return cudaGetLastError();
-}
-
-uint32_t batch_cutoff()
-{
-    if (const char* v = std::getenv("IMIN_TIER0_VERTICES"); v && *v)
-        return static_cast<uint32_t>(std::strtoul(v, nullptr, 10));
-    return kDefaultCutoff;
 }
 
 cudaError_t launch_batch_unblock(const BatchStep& B, cudaStream_t s)
@@ -376,8 +377,13 @@ cudaError_t launch_batch_cta(const BatchStep& B, const CtaCfg& c, uint32_t block
 {
     CtaCfg cfg = c;
     cfg.scratch = scratch;
-    if (c.global_bitmap) k_batch_cta<false><<<blocks, kCtaThreads, smem, s>>>(B, cfg);
-    else k_batch_cta<true><<<blocks, kCtaThreads, smem, s>>>(B, cfg);
+    if (c.global_bitmap) {
+        if (B.all_ic) k_batch_cta<false, kModelIC><<<blocks, kCtaThreads, smem, s>>>(B, cfg);
+        else k_batch_cta<false, kModelAny><<<blocks, kCtaThreads, smem, s>>>(B, cfg);
+    } else {
+        if (B.all_ic) k_batch_cta<true, kModelIC><<<blocks, kCtaThreads, smem, s>>>(B, cfg);
+        else k_batch_cta<true, kModelAny><<<blocks, kCtaThreads, smem, s>>>(B, cfg);
+    }
     return cudaGetLastError();
 }
 

@@ -88,12 +88,17 @@ __device__ __forceinline__ uint32_t vertex_word(uint32_t v, uint32_t j, uint32_t
     return k == 0 ? r.x : (k == 1 ? r.y : (k == 2 ? r.z : r.w));
 }
 
+// Propagation model of a kernel instantiation: IC or LT fixed at compile time, or taken from the
+// graph at run time (batched kernels, whose queries may mix models).
+enum : int { kModelIC = 0, kModelLT = 1, kModelAny = 2 };
+
 // Live mask (bit k: edge 4q + k) of the edges 4q .. 4q+3 that lie in [beg, end), in sample j of
 // call `round`; th = thr4[q].
 //   IC (Def. 4): edge e is live iff its Philox word (counter (q, j, round, 0), word e & 3) <= thr.
 //   LT (Sec. 4.5, linear-threshold triggering sets): edge e = (u, v) is live iff v's word lies in
 //   e's interval [lo, lo + thr], i.e. (word - lo) mod 2^32 <= thr; the in-edges of v hold disjoint
 //   intervals, so at most one of them is live.
+template <int M = kModelAny>
 __device__ __forceinline__ uint32_t group_live(const DevGraph& g, uint32_t q, const uint4& th, int32_t beg,
                                                int32_t end, uint32_t j, uint32_t round, uint32_t k0,
                                                uint32_t k1)
@@ -102,7 +107,7 @@ __device__ __forceinline__ uint32_t group_live(const DevGraph& g, uint32_t q, co
     uint32_t in = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) in |= (e0 + k >= beg && e0 + k < end) ? (1u << k) : 0u;
-    if (g.lo4 == nullptr) {
+    if (M == kModelIC || (M == kModelAny && g.lo4 == nullptr)) {
         const uint4 r = philox4x32_10(make_uint4(q, j, round, 0u), k0, k1);
         const uint32_t m = (r.x <= th.x ? 1u : 0u) | (r.y <= th.y ? 2u : 0u) | (r.z <= th.z ? 4u : 0u) |
                            (r.w <= th.w ? 8u : 0u);
@@ -143,7 +148,17 @@ struct SampleParams {
     uint32_t* lists;               // [kTiers*theta]: input list of tier t at lists + t*theta
     const int32_t* done;           // optional stop flag (GreedyReplace phase 2)
     unsigned long long* stats;     // optional [kStCount] (per-tier slots)
+    const int32_t* extra;          // spread of blocker sets: vertices blocked in this sample on
+    uint32_t n_extra;              // top of excl (nullptr / 0 otherwise)
 };
+
+// Whether v is one of the sample's extra blocked vertices (a handful at most).
+__device__ __forceinline__ bool extra_blocked(const SampleParams& P, uint32_t v)
+{
+    for (uint32_t i = 0; i < P.n_extra; ++i)
+        if (static_cast<uint32_t>(P.extra[i]) == v) return true;
+    return false;
+}
 
 // Capacities of one tier's per-warp working set.
 struct TierCfg {
@@ -225,6 +240,7 @@ struct BatchStep {
     uint2* over;                       // (query, sample) overflow items
     uint32_t over_cap;
     unsigned long long* stats;
+    uint32_t all_ic;                   // 1: every query's graph uses the IC model
 };
 
 // Byte layout of one warp's working set (same for shared and global memory).
@@ -307,7 +323,7 @@ enum SampleResult { kSampleDone = 0, kSampleOverflow = 1, kSampleError = 2 };
 
 // Runs sample j of call P.round in warp space w. kClearAll: reset the whole hash afterwards
 // (small shared tables) instead of the slots recorded in hslot[].
-template <bool G, bool kClearAll>
+template <bool G, bool kClearAll, int M = kModelAny>
 __device__ __forceinline__ int run_sample(const SampleParams& P, const WarpSpace<G>& w,
                                           uint32_t j, uint32_t lane, SampleCounters& sc)
 {
@@ -371,7 +387,7 @@ __device__ __forceinline__ int run_sample(const SampleParams& P, const WarpSpace
                 if (t < total) {
                     const uint32_t q = (static_cast<uint32_t>(o_beg) >> 2) + (t - (o_incl - o_ng));
                     const uint4 th = __ldg(P.g.thr4 + q);
-                    const uint32_t lm = group_live(P.g, q, th, o_beg, o_end, j, P.round, P.key_lo, P.key_hi);
+                    const uint32_t lm = group_live<M>(P.g, q, th, o_beg, o_end, j, P.round, P.key_lo, P.key_hi);
                     const int32_t e0 = static_cast<int32_t>(q << 2);
                     ok0 = (lm & 1u) != 0;
                     ok1 = (lm & 2u) != 0;

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <mutex>
 #include <string>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "imin_dev.cuh"
@@ -103,6 +104,13 @@ cudaError_t prepare_cta_scratch(const CtaCfg& c, uint32_t blocks, uint8_t* scrat
 cudaError_t launch_spread(const SampleParams& P, const CtaCfg& c, uint32_t blocks, uint64_t smem,
                           uint8_t* scratch, unsigned long long* sum, cudaStream_t s);
 
+// Spread of many blocker sets (spread.cu): for item i < items, adds |R| of sample i % P.theta with
+// set i / P.theta (k vertices of `sets`) blocked on top of P.excl into sums[i / P.theta].
+// *cursor must start at 0.
+cudaError_t launch_spread_sets(const SampleParams& P, const CtaCfg& c, uint32_t blocks, uint64_t smem,
+                               uint8_t* scratch, const int32_t* sets, uint32_t k, unsigned long long items,
+                               unsigned long long* cursor, unsigned long long* sums, cudaStream_t s);
+
 // Batched multi-query steps (batch.cu).
 bool plan_batch_cta(const DeviceInfo& dev, int32_t max_n, int32_t max_m, CtaCfg* c, uint32_t* blocks,
                     uint64_t* smem, uint64_t* scratch_bytes);
@@ -121,8 +129,11 @@ bool plan_batch_warp(const DeviceInfo& dev, uint32_t max_ns, uint32_t cutoff, Ti
                      uint64_t* smem);
 cudaError_t launch_batch_warp(const BatchStep& B, const TierCfg& c, uint32_t blocks, uint64_t smem,
                               cudaStream_t s);
-// Warp/block cutoff of batched steps: IMIN_TIER0_VERTICES when set, else kDefaultCutoff.
-uint32_t batch_cutoff();
+// The warp/block cutoff of one query (api.cu): IMIN_TIER0_VERTICES when set; kDefaultCutoff with
+// IMIN_AUTOTUNE=0 or on a capturing stream; otherwise the autotuner's value for the graph and the
+// seed-set size class, tuned on `s` on first use and cached.
+int tuned_cutoff(const imin_graph* g, const std::vector<int32_t>& seeds, uint64_t key, uint32_t theta_hint,
+                 cudaStream_t s, uint32_t* out);
 
 // Selection (Alg. 3/4 argmax) -----------------------------------------------------------------
 struct SelectParams {

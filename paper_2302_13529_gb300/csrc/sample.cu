@@ -41,7 +41,7 @@ uint32_t env_u32(const char* name, uint32_t dflt)
     return static_cast<uint32_t>(std::strtoul(v, nullptr, 10));
 }
 
-template <int kTier>
+template <int kTier, int M>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_sample_tier(SampleParams P, TierCfg T)
 {
@@ -90,7 +90,7 @@ k_sample_tier(SampleParams P, TierCfg T)
             from_range ? P.theta : *reinterpret_cast<const volatile uint32_t*>(&P.ctl->count[kTier]);
         if (item >= total) break;
         const uint32_t j = from_range ? item : P.lists[kTier * P.theta + item];
-        const int rc = run_sample<G, kClearAll>(P, w, j, lane, sc);
+        const int rc = run_sample<G, kClearAll, M>(P, w, j, lane, sc);
         if (rc == kSampleOverflow) {
             if (lane == 0) {
                 if (kTier < kTierWhole) {
@@ -181,8 +181,9 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns, ui
         p.scratch_bytes[0] = 0;
         int occ = 0;
         if (p.smem_bytes[0] <= dev.smem_optin) {
-            allow_max_dynamic_smem(k_sample_tier<0>, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_tier<0>,
+            allow_max_dynamic_smem(k_sample_tier<0, kModelLT>, dev);
+            allow_max_dynamic_smem(k_sample_tier<0, kModelIC>, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_tier<0, kModelIC>,
                                                           kWarpsPerBlock * 32, p.smem_bytes[0]);
         }
         p.blocks[0] = static_cast<uint32_t>(std::max(occ, 0)) * dev.sms;
@@ -240,9 +241,16 @@ cudaError_t launch_sample_tier(int tier, const SampleParams& P, const TierPlan& 
     // seed set does not fit its shared-memory working set
     c.from_range = tier == 0 || (tier == 1 && plan.blocks[0] == 0 && !plan.use_cta);
     const dim3 grid(plan.blocks[tier]), block(kWarpsPerBlock * 32);
-    if (tier == 0) k_sample_tier<0><<<grid, block, plan.smem_bytes[0], s>>>(P, c);
-    else if (tier == 1) k_sample_tier<1><<<grid, block, plan.smem_bytes[1], s>>>(P, c);
-    else k_sample_tier<2><<<grid, block, plan.smem_bytes[2], s>>>(P, c);
+    const size_t sm = plan.smem_bytes[tier];
+    if (P.g.lo4 == nullptr) {
+        if (tier == 0) k_sample_tier<0, kModelIC><<<grid, block, sm, s>>>(P, c);
+        else if (tier == 1) k_sample_tier<1, kModelIC><<<grid, block, sm, s>>>(P, c);
+        else k_sample_tier<2, kModelIC><<<grid, block, sm, s>>>(P, c);
+    } else {
+        if (tier == 0) k_sample_tier<0, kModelLT><<<grid, block, sm, s>>>(P, c);
+        else if (tier == 1) k_sample_tier<1, kModelLT><<<grid, block, sm, s>>>(P, c);
+        else k_sample_tier<2, kModelLT><<<grid, block, sm, s>>>(P, c);
+    }
     *launched = true;
     return cudaGetLastError();
 }

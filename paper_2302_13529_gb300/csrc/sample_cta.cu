@@ -18,7 +18,7 @@ using namespace cta;
 // kSmemBitmap: the visited bitmap lives in shared memory (n <= 2^18) and doubles as the
 // resolution hash; otherwise it lives in the block's global slot and the dynamic shared memory
 // holds only the resolution hash.
-template <bool kSmemBitmap>
+template <bool kSmemBitmap, int M>
 __global__ void __launch_bounds__(kCtaThreads, 8) k_sample_cta(SampleParams P, CtaCfg C)
 {
     extern __shared__ __align__(16) uint32_t dsm[];
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_sample_cta(SampleParams P, C
             C.from_list ? *reinterpret_cast<const volatile uint32_t*>(&P.ctl->count[kTierCta]) : P.theta;
         if (sh.item >= total) break;
         const uint32_t j = C.from_list ? P.lists[kTierCta * P.theta + sh.item] : sh.item;
-        const int rc = run_sample_cta<kSmemBitmap>(P, C, bm, dsm, sh, S, j, tid, sc, examined, live);
+        const int rc = run_sample_cta<kSmemBitmap, false, M>(P, C, bm, dsm, sh, S, j, tid, sc, examined, live);
         if (tid == 0) {
             if (rc == kSampleOverflow) {
                 const uint32_t pos = atomicAdd(&P.ctl->count[kTierWhole], 1u);
@@ -131,11 +131,13 @@ bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint3
     if (*smem > dev.smem_optin) return false;
     int occ = 0;
     if (smem_bitmap) {
-        allow_max_dynamic_smem(k_sample_cta<true>, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta<true>, kCtaThreads, *smem);
+        allow_max_dynamic_smem(k_sample_cta<true, kModelLT>, dev);
+        allow_max_dynamic_smem(k_sample_cta<true, kModelIC>, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta<true, kModelIC>, kCtaThreads, *smem);
     } else {
-        allow_max_dynamic_smem(k_sample_cta<false>, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta<false>, kCtaThreads, *smem);
+        allow_max_dynamic_smem(k_sample_cta<false, kModelLT>, dev);
+        allow_max_dynamic_smem(k_sample_cta<false, kModelIC>, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta<false, kModelIC>, kCtaThreads, *smem);
     }
     if (occ <= 0) return false;
     *blocks = static_cast<uint32_t>(occ) * dev.sms;
@@ -155,8 +157,14 @@ cudaError_t launch_cta_tier(const SampleParams& P, const CtaCfg& c, uint32_t blo
 {
     CtaCfg cfg = c;
     cfg.scratch = scratch;
-    if (c.global_bitmap) k_sample_cta<false><<<blocks, kCtaThreads, smem, s>>>(P, cfg);
-    else k_sample_cta<true><<<blocks, kCtaThreads, smem, s>>>(P, cfg);
+    const bool lt = P.g.lo4 != nullptr;
+    if (c.global_bitmap) {
+        if (lt) k_sample_cta<false, kModelLT><<<blocks, kCtaThreads, smem, s>>>(P, cfg);
+        else k_sample_cta<false, kModelIC><<<blocks, kCtaThreads, smem, s>>>(P, cfg);
+    } else {
+        if (lt) k_sample_cta<true, kModelLT><<<blocks, kCtaThreads, smem, s>>>(P, cfg);
+        else k_sample_cta<true, kModelIC><<<blocks, kCtaThreads, smem, s>>>(P, cfg);
+    }
     return cudaGetLastError();
 }
 

@@ -96,7 +96,7 @@ __device__ __forceinline__ void visit_staged(const SampleParams& P, const CtaCfg
             ul = c.x;
             v = static_cast<uint32_t>(__ldg(P.g.col + c.y));
             row = make_int2(__ldg(P.g.row_ptr + v), __ldg(P.g.row_ptr + v + 1));
-            if (!excluded(P.excl, v)) {
+            if (!excluded(P.excl, v) && !(kSpread && extra_blocked(P, v))) {
                 ++lv;
                 const uint32_t bit = 1u << (v & 31);
                 disc = (atomicOr(bm + (v >> 5), bit) & bit) == 0;
@@ -275,7 +275,7 @@ __device__ __forceinline__ bool finish_tree_packed(const SampleParams& P, CtaSha
 // the non-tree target resolution -- the bitmap itself when kResInBitmap (it is cleared first).
 // kSpread: only the BFS; |R| (seeds included) is added to sc.reached and the dominator step is
 // skipped (the Monte-Carlo spread estimate of Def. 3).
-template <bool kResInBitmap, bool kSpread = false>
+template <bool kResInBitmap, bool kSpread = false, int M = kModelAny>
 __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCfg& C, uint32_t* bm,
                                               uint32_t* res, CtaShared& sh, const Slot& S, uint32_t j,
                                               uint32_t tid, SampleCounters& sc,
@@ -377,7 +377,7 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
                 const uint4 th = nth;
                 fetch(t0 + kCtaThreads + tid);
                 uint32_t m = 0;
-                if (oe > ob) m = group_live(P.g, q, th, ob, oe, j, P.round, P.key_lo, P.key_hi);
+                if (oe > ob) m = group_live<M>(P.g, q, th, ob, oe, j, P.round, P.key_lo, P.key_hi);
                 const uint32_t nc = __popc(m);
                 const uint32_t cincl = warp_incl_scan(nc, lane);
                 uint32_t w = staged + cincl - nc;

@@ -48,6 +48,7 @@ struct Req {
     uint8_t* mem = nullptr;
     uint64_t off_seeds = 0, off_excl = 0, off_cb = 0, off_delta = 0, off_blk = 0, off_done = 0;
     bool warp = false;  // its samples go to the warp tier first
+    uint32_t cutoff = 0;  // its graph's tuned warp/block cutoff (set at admission)
     // result
     bool done = false;
     int status = IMIN_OK;
@@ -208,11 +209,15 @@ int imin_server::grow_plans(const std::vector<Req*>& active)
             regrow = true;
         }
     }
-    uint32_t ns_w = warp_ns;
-    for (Req* r : active)
-        if (r->warp) ns_w = std::max<uint32_t>(ns_w, static_cast<uint32_t>(r->seeds.size()));
-    if (ns_w > warp_ns) {
+    uint32_t ns_w = warp_ns, c_w = cutoff;
+    for (Req* r : active) {
+        if (!r->warp) continue;
+        ns_w = std::max<uint32_t>(ns_w, static_cast<uint32_t>(r->seeds.size()));
+        c_w = std::max(c_w, r->cutoff);
+    }
+    if (ns_w > warp_ns || c_w > cutoff) {
         warp_ns = ns_w;
+        cutoff = c_w;
         warp_ok = plan_batch_warp(dev, warp_ns, cutoff, &wcfg, &warp_blocks, &warp_smem);
     }
     if (regrow) {
@@ -259,9 +264,18 @@ void imin_server::run()
             }
         }
 
-        // set up the newly admitted requests
+        // set up the newly admitted requests; each takes its graph's tuned warp/block cutoff
+        // (tuned on this stream the first time a graph and seed-set size class is seen)
         bool need_cb = false;
         for (Req* r : admitted) {
+            if (r->warp) {
+                const int rc = tuned_cutoff(r->g, r->seeds, r->key, r->theta, s, &r->cutoff);
+                if (rc != IMIN_OK) {
+                    fail_all(rc, "warp/block cutoff tuning failed");
+                    return;
+                }
+                r->warp = r->cutoff > 0;
+            }
             SRV_CUDA(cudaMallocAsync(&r->mem, r->bytes, s));
             SRV_CUDA(cudaMemsetAsync(r->mem, 0, r->bytes, s));
             SRV_CUDA(cudaMemcpyAsync(r->mem + r->off_seeds, r->seeds.data(), 4ull * r->seeds.size(),
@@ -361,6 +375,8 @@ void imin_server::run()
             B.over_cap = static_cast<uint32_t>(std::min<uint64_t>(over_cap, 0xFFFFFFFFull));
             B.stats = nullptr;
             B.prefix = dprefix;
+            B.all_ic = 1;
+            for (Req* r : active) B.all_ic = B.all_ic && r->g->model == 0 ? 1u : 0u;
             // every slot follows its own driver's schedule (BatchQuery::gr)
             if (any_gr) SRV_CUDA(launch_batch_unblock(B, s));
             if (class_busy[kBatchClasses]) {
@@ -431,7 +447,7 @@ int imin_server_create(const imin_server_config* cfg, imin_server** out)
     cudaMemGetInfo(&free_b, &total_b);
     srv->budget = (cfg && cfg->memory_budget) ? cfg->memory_budget : static_cast<uint64_t>(free_b / 4);
     srv->max_active = (cfg && cfg->max_active > 0) ? cfg->max_active : 256;
-    srv->cutoff = batch_cutoff();
+    srv->cutoff = 0;
     srv->slots.assign(srv->max_active, nullptr);
     const size_t stride = static_cast<size_t>(srv->max_active) + 1;
     cudaError_t e = cudaStreamCreateWithFlags(&srv->s, cudaStreamNonBlocking);
@@ -492,7 +508,7 @@ int imin_server_submit(imin_server* srv, int32_t driver, const imin_graph* g, co
         }
         mark[v] = 1;
     }
-    plan_request(*r, srv->cutoff);
+    plan_request(*r, 1);  // room for the warp tier's done flags; admission decides whether it runs
     if (r->bytes > srv->budget) {
         delete r;
         return fail_msg(IMIN_ERR_NOMEM, "the request's device state exceeds the server's memory budget");

@@ -65,7 +65,72 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_spread_cta(SampleParams P, C
     }
 }
 
+// The simulated spread of many blocker sets (the comparison algorithms of Sec. 5 -- BaselineGreedy,
+// Exact -- score candidate sets this way): work item i is (set i / theta, sample i % theta); the
+// sample runs with the set's k vertices blocked on top of excl, and its |R| (seeds included) is
+// added to sums[set]. Every set sees the same samples (common random numbers).
+template <bool kSmemBitmap>
+__global__ void __launch_bounds__(kCtaThreads, 8) k_spread_sets(SampleParams P, CtaCfg C, const int32_t* sets,
+                                                                uint32_t k, unsigned long long items,
+                                                                unsigned long long* cursor,
+                                                                unsigned long long* sums)
+{
+    extern __shared__ __align__(16) uint32_t dsm[];
+    __shared__ CtaShared sh;
+    __shared__ unsigned long long s_item;
+    const uint32_t tid = threadIdx.x;
+    uint8_t* base = C.scratch + static_cast<uint64_t>(blockIdx.x) * C.slot_bytes;
+    Slot S;
+    S.gid = reinterpret_cast<int32_t*>(base + C.off_gid);
+    S.par = reinterpret_cast<uint32_t*>(base + C.off_par);
+    S.idom = reinterpret_cast<uint32_t*>(base + C.off_idom);
+    S.rows = reinterpret_cast<int2*>(base + C.off_rows);
+    S.edges = reinterpret_cast<uint2*>(base + C.off_edges);
+    uint32_t* bm = kSmemBitmap ? dsm : reinterpret_cast<uint32_t*>(base + C.off_bm);
+    if constexpr (kSmemBitmap) {
+        for (uint32_t i = tid; i < C.bm_words; i += kCtaThreads) bm[i] = 0;
+    }
+    SampleCounters sc;
+    unsigned long long examined = 0, live = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(cursor, 1ull);
+        __syncthreads();
+        const unsigned long long item = s_item;
+        if (item >= items) break;
+        const uint32_t set = static_cast<uint32_t>(item / P.theta);
+        const uint32_t j = static_cast<uint32_t>(item % P.theta);
+        SampleParams Q = P;
+        Q.extra = sets + static_cast<uint64_t>(set) * k;
+        Q.n_extra = k;
+        const unsigned long long before = sc.reached;
+        const int rc = run_sample_cta<kSmemBitmap, true>(Q, C, bm, dsm, sh, S, j, tid, sc, examined, live);
+        if (tid == 0) {
+            if (rc != kSampleDone) atomicOr(&P.ctl->error, rc == kSampleOverflow ? kErrCapacity : kErrInternal);
+            else atomicAdd(sums + set, sc.reached - before);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_spread_sets(const SampleParams& P, const CtaCfg& c, uint32_t blocks, uint64_t smem,
+                               uint8_t* scratch, const int32_t* sets, uint32_t k, unsigned long long items,
+                               unsigned long long* cursor, unsigned long long* sums, cudaStream_t s)
+{
+    CtaCfg cfg = c;
+    cfg.scratch = scratch;
+    cfg.from_list = 0;
+    const DeviceInfo dev = device_info();
+    if (c.global_bitmap) {
+        allow_max_dynamic_smem(k_spread_sets<false>, dev);
+        k_spread_sets<false><<<blocks, kCtaThreads, smem, s>>>(P, cfg, sets, k, items, cursor, sums);
+    } else {
+        allow_max_dynamic_smem(k_spread_sets<true>, dev);
+        k_spread_sets<true><<<blocks, kCtaThreads, smem, s>>>(P, cfg, sets, k, items, cursor, sums);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_spread(const SampleParams& P, const CtaCfg& c, uint32_t blocks, uint64_t smem,
                           uint8_t* scratch, unsigned long long* sum, cudaStream_t s)

@@ -96,6 +96,14 @@ def lib():
         L.imin_estimate_spread.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_uint32,
                                            ctypes.c_uint64, ctypes.c_uint32,
                                            ctypes.POINTER(ctypes.c_uint64), P]
+        L.imin_estimate_spread_sets.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int32, P, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64,
+                                                ctypes.c_uint32, P, P]
+        for name in ("imin_baseline_greedy", "imin_exact_blockers"):
+            getattr(L, name).argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
+                                         ctypes.c_uint64, P, P, P]
+        L.imin_out_degree_blockers.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, P, P]
+        L.imin_random_blockers.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, P, P]
         for name in ("imin_batch_advanced_greedy", "imin_batch_greedy_replace"):
             getattr(L, name).argtypes = [ctypes.POINTER(Query), ctypes.c_int32, P]
         L.imin_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
@@ -256,6 +264,51 @@ def advanced_greedy(gh: GraphHandle, seeds, b, theta, key, out=None, stream=None
 def greedy_replace(gh: GraphHandle, seeds, b, theta, key, out=None, stream=None):
     """imin_greedy_replace (Alg. 4): blockers in list order."""
     return _greedy(lib().imin_greedy_replace, gh, seeds, b, theta, key, out, stream)
+
+
+def estimate_spread_sets(gh: GraphHandle, seeds, blocked, sets, theta, key, round_=0, stream=None):
+    """imin_estimate_spread_sets: uint64[len(sets)], the simulated spread sum of each blocker set
+    (a row of `sets`, blocked on top of `blocked`) over the same theta sampled graphs."""
+    s, ks, ns = _ptr(seeds, np.int32)
+    b, kb, nb = _ptr(blocked if blocked is not None and len(blocked) else None, np.int32)
+    arr = np.ascontiguousarray(np.asarray(sets, dtype=np.int32).reshape(len(sets), -1))
+    k = int(arr.shape[1]) if len(sets) else 0
+    st, kst, _ = _ptr(arr.reshape(-1) if arr.size else None, np.int32)
+    out = np.zeros(max(len(sets), 1), dtype=np.uint64)
+    o, ko, _ = _ptr(out, np.uint64)
+    _check(lib().imin_estimate_spread_sets(gh.handle, s, ns, b, nb, st, len(sets), k, int(theta), int(key),
+                                           int(round_), o, _stream(stream)))
+    return out[:len(sets)]
+
+
+def baseline_greedy(gh: GraphHandle, seeds, b, r, key, out=None, stream=None):
+    """imin_baseline_greedy (Alg. 1 with r-sample simulations per candidate)."""
+    return _greedy(lib().imin_baseline_greedy, gh, seeds, b, r, key, out, stream)
+
+
+def exact_blockers(gh: GraphHandle, seeds, b, r, key, out=None, stream=None):
+    """imin_exact_blockers: the b-subset of V \\ S with the smallest simulated spread."""
+    return _greedy(lib().imin_exact_blockers, gh, seeds, b, r, key, out, stream)
+
+
+def out_degree_blockers(gh: GraphHandle, seeds, b):
+    """imin_out_degree_blockers (OutDegree)."""
+    s, ks, ns = _ptr(seeds, np.int32)
+    out = np.zeros(max(int(b), 1), dtype=np.int32)
+    cnt = ctypes.c_int32()
+    _check(lib().imin_out_degree_blockers(gh.handle, s, ns, int(b), out.ctypes.data_as(ctypes.c_void_p),
+                                          ctypes.byref(cnt)))
+    return out[:cnt.value]
+
+
+def random_blockers(gh: GraphHandle, seeds, b, key):
+    """imin_random_blockers (Rand)."""
+    s, ks, ns = _ptr(seeds, np.int32)
+    out = np.zeros(max(int(b), 1), dtype=np.int32)
+    cnt = ctypes.c_int32()
+    _check(lib().imin_random_blockers(gh.handle, s, ns, int(b), int(key), out.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.byref(cnt)))
+    return out[:cnt.value]
 
 
 def _batch(fn, items, stream):
