@@ -14,7 +14,11 @@ The same line carries the metric's other quantities, each measured in this run (
                     (samples/s of both, their ratio, bit-exactness of every result);
   large_query       R-MAT n=2^22, m=2^26, |S|=200, b=200, theta=2*10^5: AG and GR wall time;
   serving           a Poisson request stream on the R-MAT 2^17 and 2^22 graphs: p50/p99 latency
-                    and samples/s against serving the same requests one at a time.
+                    and samples/s against serving the same requests one at a time;
+  quality           the paper's quality studies on synthetic stand-ins: GreedyReplace's expected
+                    spread and time for theta in {10^3, 10^4, 10^5}; Exact vs GreedyReplace on
+                    100-vertex graphs (b = 1..3); BaselineGreedy (Alg. 1) vs AdvancedGreedy and
+                    GreedyReplace time at b = 10.
 
 Under torchrun (N > 1) every rank runs an independent replica of the headline query on its own
 GPU (the path has no exchange step); value = samples of all ranks / the slowest rank's time.
@@ -60,9 +64,11 @@ def parse_args(argv=None):
                    help="--impl reference: target host time of one step (a bounded sample)")
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="target CPU time of each oracle baseline sample")
-    p.add_argument("--workload", choices=("rmat17", "batch256", "serving", "rmat22"), default="rmat17",
+    p.add_argument("--workload", choices=("rmat17", "batch256", "serving", "rmat22", "quality"),
+                   default="rmat17",
                    help="rmat17: the full line (headline plus the other legs); batch256, serving, "
-                        "rmat22: one leg alone, printed as its own line")
+                        "rmat22: one leg alone, printed as its own line; quality: the theta sweep, "
+                        "Exact vs GreedyReplace and BaselineGreedy vs AdvancedGreedy studies")
     p.add_argument("--requests", type=int, default=16,
                    help="serving: number of requests (the full configuration has 2,000)")
     p.add_argument("--b", type=int, default=None,
@@ -533,8 +539,119 @@ def leg_serving(requests: int, seed: int = 5000) -> dict:
             "server": st}
 
 
+def leg_theta_sweep(eval_theta: int = 100_000) -> dict:
+    """The paper's theta sensitivity study (Sec. 5, "Varying the Number of Sampled Graphs": TR
+    model, b = 20, 10 random seeds, theta in {10^3, 10^4, 10^5}, GreedyReplace's expected spread
+    and running time) on two synthetic stand-ins: R-MAT 2^17 / 2^20 and Chung-Lu n = 10^5,
+    m = 10^6, both with TR probabilities. Each blocker set's spread is simulated with
+    `eval_theta` samples on an independent key; the decrease ratio is spread(theta_prev) /
+    spread(theta) - 1."""
+    import numpy as np
+    import torch
+    from paper_2302_13529_gb300 import imin, workloads as W
+
+    rp, col = W.rmat(17, 1 << 20, W.RMAT_ABCD, 1102)
+    g1 = W.Graph(1 << 17, rp, col, W.tr_thresholds(len(col), 1103), "rmat17-tr")
+    rp, col = W.chung_lu(100_000, 1_000_000, 2.1, 1104)
+    g2 = W.Graph(100_000, rp, col, W.tr_thresholds(len(col), 1105), "chunglu-1e5-tr")
+    out = {"model": "TR", "b": 20, "seeds": 10, "eval_theta": eval_theta, "graphs": {}}
+    for g in (g1, g2):
+        gh = imin.load_graph(g)
+        seeds = W.uniform_seeds(g.n, 10, 1106)
+        key = W.query_key(1107)
+        ev_key = W.query_key(1108)
+        rows, prev = [], None
+        imin.greedy_replace(gh, seeds, 20, 1000, key)  # warm-up and cutoff tuning
+        for theta in (1000, 10_000, 100_000):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            B = imin.greedy_replace(gh, seeds, 20, theta, key)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t
+            sp = imin.estimate_spread(gh, seeds, B, eval_theta, ev_key) / eval_theta
+            rows.append({"theta": theta, "gr_seconds": secs, "expected_spread": sp,
+                         "decrease_ratio_vs_previous": (prev / sp - 1.0) if prev else None})
+            prev = sp
+        out["graphs"][g.name] = {"n": g.n, "m": g.m, "runs": rows,
+                                 "no_blockers_spread": imin.estimate_spread(gh, seeds, [], eval_theta, ev_key)
+                                 / eval_theta}
+        gh.close()
+    return out
+
+
+def leg_exact_small(bmax: int = 3, r: int = 10_000) -> dict:
+    """Exact vs GreedyReplace on small graphs (the paper's Tables 5-6 compare them on 100-vertex
+    extracts of EmailCore with 10 random seeds and theta = r = 10^4, TR and WC): a directed
+    Chung-Lu graph with n = 100, m = 800 under TR and WC, 10 seeds, b = 1..bmax; the spread of
+    each result simulated with 10^5 samples on an independent key, and both running times."""
+    import torch
+    from paper_2302_13529_gb300 import imin, workloads as W
+
+    rp, col = W.chung_lu(100, 800, 2.1, 1201)
+    graphs = {"TR": W.Graph(100, rp, col, W.tr_thresholds(len(col), 1202)),
+              "WC": W.Graph(100, rp, col, W.wc_thresholds(col, 100))}
+    seeds = W.uniform_seeds(100, 10, 1203)
+    key, ev_key = W.query_key(1204), W.query_key(1205)
+    out = {"n": 100, "m": 800, "seeds": 10, "r": r, "theta": r, "models": {}}
+    for name, g in graphs.items():
+        gh = imin.load_graph(g)
+        imin.greedy_replace(gh, seeds, 1, 1000, key)
+        rows = []
+        for b in range(1, bmax + 1):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            E = imin.exact_blockers(gh, seeds, b, r, key)
+            torch.cuda.synchronize()
+            t_exact = time.perf_counter() - t
+            t = time.perf_counter()
+            G = imin.greedy_replace(gh, seeds, b, r, key)
+            torch.cuda.synchronize()
+            t_gr = time.perf_counter() - t
+            se = imin.estimate_spread(gh, seeds, E, 100_000, ev_key) / 1e5
+            sg = imin.estimate_spread(gh, seeds, G, 100_000, ev_key) / 1e5
+            rows.append({"b": b, "exact_seconds": t_exact, "gr_seconds": t_gr, "exact_spread": se,
+                         "gr_spread": sg, "gr_over_exact_spread": sg / se,
+                         "exact": [int(x) for x in E], "gr": [int(x) for x in G]})
+        out["models"][name] = rows
+        gh.close()
+    return out
+
+
+def leg_baseline_greedy(b: int = 10, r: int = 10_000) -> dict:
+    """AdvancedGreedy and GreedyReplace against BaselineGreedy (Alg. 1, every candidate scored by
+    r simulations per round) on the small Chung-Lu workload (n = 2,000, m = 10^4, WC, |S| = 10),
+    b rounds, theta = r; the paper reports AG and GR >= 3 orders of magnitude faster at b = 10.
+    BaselineGreedy must return AdvancedGreedy's list (the same samples, Cor. 1)."""
+    import torch
+    from paper_2302_13529_gb300 import imin, workloads as W
+
+    q = W.tiny_chung_lu_query()
+    gh = imin.load_graph(q.graph)
+    imin.advanced_greedy(gh, q.seeds, 1, 1000, q.key)
+    times, res = {}, {}
+    for name, fn in (("baseline_greedy", imin.baseline_greedy), ("advanced_greedy", imin.advanced_greedy),
+                     ("greedy_replace", imin.greedy_replace)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res[name] = [int(x) for x in fn(gh, q.seeds, b, r, q.key)]
+        torch.cuda.synchronize()
+        times[name] = time.perf_counter() - t
+    gh.close()
+    return {"graph": "chunglu n=2000 m=10000 WC", "seeds": 10, "b": b, "r": r, "seconds": times,
+            "speedup_ag_over_bg": times["baseline_greedy"] / times["advanced_greedy"],
+            "speedup_gr_over_bg": times["baseline_greedy"] / times["greedy_replace"],
+            "bg_equals_ag": res["baseline_greedy"] == res["advanced_greedy"]}
+
+
 def leg_line(name: str, leg: dict, world: int) -> dict:
-    """A leg run alone (--workload batch256 / rmat22 / serving), as its own bench line."""
+    """A leg run alone (--workload batch256 / rmat22 / serving / quality), as its own bench line."""
+    if name == "quality":
+        bg = leg["baseline_greedy"]
+        return {"metric": METRIC, "value": 1.0 / bg["seconds"]["advanced_greedy"], "unit": "queries/s",
+                "n_gpus": world, "steps": 1, "warmup": 1,
+                "ms_per_step": 1e3 * bg["seconds"]["advanced_greedy"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "uint32", "data": "synthetic",
+                "config": {"workload": "quality-studies"}, name: leg}
     if name == "batch256":
         v, ms = leg["batched"]["value"], 1e3 * leg["batched"]["seconds"]
     elif name == "rmat22":
@@ -584,7 +701,9 @@ def main(argv=None):
     if args.workload != "rmat17":
         leg = {"batch256": lambda: leg_batch(max(args.steps, 1), args.warmup, rank),
                "rmat22": lambda: leg_rmat22(args.b, args.theta, rank),
-               "serving": lambda: leg_serving(args.requests, 5000 + rank)}[args.workload]()
+               "serving": lambda: leg_serving(args.requests, 5000 + rank),
+               "quality": lambda: {"theta_sweep": leg_theta_sweep(), "exact_small": leg_exact_small(),
+                                   "baseline_greedy": leg_baseline_greedy()}}[args.workload]()
         if rank == 0:
             print(json.dumps(leg_line(args.workload, leg, world)), flush=True)
         return
@@ -719,6 +838,8 @@ def main(argv=None):
         line["batched_vs_plain"] = leg_batch(2, 1)
         line["large_query"] = leg_rmat22()
         line["serving"] = leg_serving(args.requests)
+        line["quality"] = {"theta_sweep": leg_theta_sweep(), "exact_small": leg_exact_small(),
+                           "baseline_greedy": leg_baseline_greedy()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(q, args.cpu_seconds)
     if rank == 0:
