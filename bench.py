@@ -212,9 +212,9 @@ def profile_fields(kernel: str, workload: str = WORKLOAD) -> dict:
         return {}
     out = {}
     for line in open(path):
-        if ":" in line and not line.startswith(("#", "|", " ", "*", "`")):
-            k, v = line.split(":", 1)
-            out[k.strip()] = v.strip()
+        k, sep, v = line.partition(":")
+        if sep and k and all(c.islower() or c == "_" for c in k):
+            out[k] = v.strip()
     return out
 
 
@@ -468,9 +468,15 @@ def leg_rmat22(b=None, theta=None, key_offset: int = 0) -> dict:
 def leg_serving(requests: int, seed: int = 5000) -> dict:
     """Requests against the R-MAT 2^17 (m=2^20) and R-MAT 2^22 (m=2^26) WC graphs held resident:
     each picks a graph with probability 1/2, |S| ~ U[10, 500], b ~ U[10, 100],
-    theta ~ U[1e4, 1e5] (AdvancedGreedy). A burst (all requests at once) measures the saturation
-    rate; a replay with Poisson arrivals at 80 % of that rate gives p50/p99 latency and samples/s;
-    the serial baseline runs every third request one query at a time."""
+    theta ~ U[1e4, 1e5] (AdvancedGreedy).
+      serial   every request run alone, one after another (imin_advanced_greedy): its service
+               time and the saturated serial throughput;
+      burst    all requests submitted at once to the continuous-batching server: its saturated
+               throughput;
+      poisson  the same requests with Poisson arrivals at 80 % of the serial saturation rate,
+               through the server (latency p50/p99), and through a one-at-a-time FIFO queue
+               whose latencies follow from the same arrival times and the measured service
+               times (finish_i = max(arrival_i, finish_{i-1}) + service_i)."""
     import threading
 
     import numpy as np
@@ -483,14 +489,13 @@ def leg_serving(requests: int, seed: int = 5000) -> dict:
     samples = sum(r.b * r.theta for r in reqs)
 
     def serve(arrivals):
-        todo = reqs[:len(arrivals)]
-        lat = [None] * len(todo)
+        lat = [None] * len(reqs)
         with imin.Server() as srv:
             t0 = time.perf_counter()
-            tickets = [None] * len(todo)
+            tickets = [None] * len(reqs)
 
             def submitter():
-                for i, r in enumerate(todo):
+                for i, r in enumerate(reqs):
                     wait = arrivals[i] - (time.perf_counter() - t0)
                     if wait > 0:
                         time.sleep(wait)
@@ -499,43 +504,47 @@ def leg_serving(requests: int, seed: int = 5000) -> dict:
             th = threading.Thread(target=submitter)
             th.start()
             th.join()
-            for i, r in enumerate(todo):
+            for i, r in enumerate(reqs):
                 _, lat[i] = srv.wait(tickets[i], capacity=r.b)
             elapsed = time.perf_counter() - t0
             st = srv.stats()
         return elapsed, np.array(lat), st
 
-    serve([0.0] * min(len(reqs), 2))  # warm-up (module load, first plans)
-    burst_s, burst_lat, _ = serve([0.0] * len(reqs))
-    rate = 0.8 * len(reqs) / burst_s  # requests per second at 80 % of saturation
-    gaps = np.random.default_rng(seed + 1000).exponential(1.0 / rate, size=len(reqs))
-    poisson_s, lat, st = serve(list(np.cumsum(gaps) - gaps[0]))
-    sub_ids = list(range(0, len(reqs), 3))
-    for i in sub_ids:  # the plain calls' cutoff tuning (per seed-set size class) stays out of their timing
-        r = reqs[i]
+    for r in reqs:  # every graph / seed-set size class tuned before anything is timed
         imin.advanced_greedy(hs[r.gi], r.seeds, 1, 1000, r.key)
     torch.cuda.synchronize()
-    t = time.perf_counter()
-    for i in sub_ids:
-        r = reqs[i]
+    service = []
+    for r in reqs:
+        t = time.perf_counter()
         imin.advanced_greedy(hs[r.gi], r.seeds, r.b, r.theta, r.key)
-    torch.cuda.synchronize()
-    serial_s = time.perf_counter() - t
-    serial_samples = sum(reqs[i].b * reqs[i].theta for i in sub_ids)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t)
+    serial_s = sum(service)
+    burst_s, burst_lat, _ = serve([0.0] * len(reqs))
+    rate = 0.8 * len(reqs) / serial_s  # requests per second at 80 % of serial saturation
+    gaps = np.random.default_rng(seed + 1000).exponential(1.0 / rate, size=len(reqs))
+    arrivals = np.cumsum(gaps) - gaps[0]
+    poisson_s, lat, st = serve(list(arrivals))
+    fifo, finish = [], 0.0
+    for a, sv in zip(arrivals, service):
+        finish = max(a, finish) + sv
+        fifo.append(1e3 * (finish - a))
+    fifo = np.array(fifo)
     for h in hs:
         h.close()
+    pct = lambda a, p: float(np.percentile(a, p))
     return {"workload": "serving-rmat17-rmat22-advanced-greedy", "requests": len(reqs),
-            "full_configuration_requests": 2000,
-            "arrivals": f"Poisson at 80% of the burst rate ({rate:.3f} req/s)", "samples": samples,
+            "full_configuration_requests": 2000, "samples": samples,
             "value": samples / poisson_s, "unit": "samples/s", "seconds": poisson_s,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max())},
+            "arrivals": f"Poisson at 80% of the serial saturation rate ({rate:.3f} req/s)",
+            "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": float(lat.max())},
+            "fifo_serial_latency_ms": {"p50": pct(fifo, 50), "p99": pct(fifo, 99), "max": float(fifo.max())},
             "burst": {"seconds": burst_s, "samples_per_s": samples / burst_s,
-                      "p50_ms": float(np.percentile(burst_lat, 50)),
-                      "p99_ms": float(np.percentile(burst_lat, 99))},
-            "serial_one_query_at_a_time": {"value": serial_samples / serial_s, "unit": "samples/s",
-                                           "requests": len(sub_ids)},
-            "poisson_over_serial": (samples / poisson_s) / (serial_samples / serial_s),
+                      "p50_ms": pct(burst_lat, 50), "p99_ms": pct(burst_lat, 99)},
+            "serial_one_query_at_a_time": {"value": samples / serial_s, "unit": "samples/s",
+                                           "seconds": serial_s, "requests": len(reqs)},
+            "burst_over_serial": serial_s / burst_s,
+            "p99_serial_over_server": pct(fifo, 99) / pct(lat, 99),
             "server": st}
 
 
