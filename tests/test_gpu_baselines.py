@@ -88,3 +88,30 @@ def test_sets_are_validated(cuda_lib):
         with pytest.raises(IminError) as e:
             cuda_lib.estimate_spread_sets(gh, [0], [2], sets, 10, 1)
         assert e.value.code == -1
+
+
+def test_comparison_algorithms_reject_bad_arguments_and_take_device_buffers(cuda_lib):
+    import torch
+    from paper_2302_13529_gb300.imin import IminError
+    q = W.tiny_chung_lu_query()
+    gh = cuda_lib.load_graph(q.graph)
+    for f in (cuda_lib.baseline_greedy, cuda_lib.exact_blockers):
+        with pytest.raises(IminError):
+            f(gh, q.seeds, -1, 10, 1)
+        with pytest.raises(IminError):
+            f(gh, q.seeds, 1, 0, 1)  # r = 0
+        assert len(f(gh, q.seeds, 0, 10, 1)) == 0
+    with pytest.raises(IminError):
+        cuda_lib.exact_blockers(gh, q.seeds, 6, 10, 1)  # C(1990, 6) sets: beyond the limit
+    # device seeds, sets and output
+    rest = np.setdiff1d(np.arange(q.graph.n), q.seeds)[:16].astype(np.int32)
+    sets_d = torch.from_numpy(rest.reshape(8, 2)).cuda()
+    out_d = torch.zeros(8, dtype=torch.uint64, device="cuda")
+    seeds_d = torch.from_numpy(q.seeds).cuda()
+    s_ptr = cuda_lib._ptr(sets_d, np.int32)[0]
+    o_ptr = cuda_lib._ptr(out_d, np.uint64)[0]
+    sd_ptr = cuda_lib._ptr(seeds_d, np.int32)[0]
+    rc = cuda_lib.lib().imin_estimate_spread_sets(gh.handle, sd_ptr, len(q.seeds), None, 0, s_ptr, 8, 2, 500,
+                                                  q.key, 2, o_ptr, cuda_lib._stream(None))
+    assert rc == 0
+    assert np.array_equal(out_d.cpu().numpy(), O.spread_sets(q.graph, q.seeds, [], rest.reshape(8, 2), 500, q.key, 2))

@@ -47,6 +47,18 @@ def test_no_alloc_matches_regular_entry_point(cuda_lib):
         assert np.array_equal(out.cpu().numpy(), want), rnd
 
 
+def test_no_alloc_on_a_linear_threshold_graph(cuda_lib):
+    """The same call on a graph loaded under the linear-threshold model: equal to the regular
+    entry point and to the oracle's LT mode."""
+    q = W.tiny_chung_lu_query()
+    g = W.Graph(q.graph.n, q.graph.row_ptr, q.graph.col, W.lt_wc_weights(q.graph.col, q.graph.n))
+    gh = cuda_lib.load_graph(g, model="lt")
+    for rnd, theta in ((0, 3000), (5, 2000)):
+        got = cuda_lib.estimate_decrease_noalloc(gh, q.seeds, [], theta, q.key, rnd)
+        assert np.array_equal(got, cuda_lib.estimate_decrease(gh, q.seeds, [], theta, q.key, rnd))
+        assert np.array_equal(got, O.decrease(g, q.seeds, [], theta, q.key, rnd, model="lt"))
+
+
 def test_no_alloc_rejects_requests_beyond_its_limits(cuda_lib):
     from paper_2302_13529_gb300.imin import IminError
     q = W.tiny_chung_lu_query()
