@@ -229,7 +229,8 @@ int imin_estimate_decrease_noalloc(const imin_graph* g, const int32_t* seeds, in
  * imin_advanced_greedy / imin_greedy_replace return for it alone (same random streams, same
  * round numbering, same tie rule). Graphs must all live on the current device. Queries are
  * grouped by graph size so that each group's launch reserves only the memory its largest graph
- * needs. */
+ * needs. Each query takes the warp/block cutoff imin_autotune picks for its graph and seed-set
+ * size class (tuned on `stream` on first use and cached, as for the single-query calls). */
 typedef struct imin_query {
     const imin_graph* graph;  /* in: loaded graph */
     const int32_t* seeds;     /* in: n_seeds distinct vertex ids (host or device) */
@@ -257,7 +258,9 @@ int imin_batch_greedy_replace(imin_query* queries, int32_t n_queries, void* stre
  * every admitted request, then one selection launch); a request admitted at step t runs its own
  * rounds 0, 1, ... at steps t, t+1, ..., so its random stream and result are exactly those of
  * imin_advanced_greedy / imin_greedy_replace called alone. Finished requests leave between
- * steps and free their slot and memory. Graphs must stay loaded until their requests finish. */
+ * steps and free their slot and memory. Graphs must stay loaded until their requests finish.
+ * At admission each request takes its graph's tuned warp/block cutoff (tuned on the server's
+ * stream the first time a graph and seed-set size class is seen). */
 typedef struct imin_server imin_server;
 
 typedef struct imin_server_config {
