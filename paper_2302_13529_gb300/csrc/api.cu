@@ -1101,10 +1101,11 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
 
     // per-step item prefixes: one row per size class (queries of other classes and inactive
     // ones contribute no items) and one row, kRows - 1, for the warp tier
-    // queue granularity: samples per work item, about 16 items per resident block of a step, at
-    // most 64 (IMIN_BATCH_CHUNK overrides it for measurements)
+    // queue granularity: samples per work item, about 16 items per resident block of a step and
+    // at most 16 (measured on the 256-query batch: 16 samples per item 0.912 s, 4: 0.924 s,
+    // 32: 0.926 s, 64: 0.978 s, 128: 1.095 s; IMIN_BATCH_CHUNK overrides it for measurements)
     uint32_t chunk = static_cast<uint32_t>(std::max<uint64_t>(
-        1, std::min<uint64_t>(64, sum_theta / (static_cast<uint64_t>(cta_blocks[0] + cta_blocks[1] +
+        1, std::min<uint64_t>(16, sum_theta / (static_cast<uint64_t>(cta_blocks[0] + cta_blocks[1] +
                                                                      cta_blocks[2] + cta_blocks[3]) * 16 + 1))));
     if (const char* v = std::getenv("IMIN_BATCH_CHUNK"); v && *v)
         chunk = std::max<uint32_t>(1, static_cast<uint32_t>(std::strtoul(v, nullptr, 10)));
