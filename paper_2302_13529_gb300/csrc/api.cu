@@ -364,8 +364,6 @@ SampleParams sample_params(const imin_graph* g, const Query& q, uint32_t ns, uin
     P.lists = q.lists;
     P.done = done;
     P.stats = q.stats;
-    P.extra = nullptr;
-    P.n_extra = 0;
     return P;
 }
 

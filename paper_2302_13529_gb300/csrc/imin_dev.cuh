@@ -151,15 +151,20 @@ struct SampleParams {
     uint32_t* lists;               // [kTiers*theta]: input list of tier t at lists + t*theta
     const int32_t* done;           // optional stop flag (GreedyReplace phase 2)
     unsigned long long* stats;     // optional [kStCount] (per-tier slots)
-    const int32_t* extra;          // spread of blocker sets: vertices blocked in this sample on
-    uint32_t n_extra;              // top of excl (nullptr / 0 otherwise)
+};
+
+// Vertices blocked in one sample on top of excl (the spread of blocker sets scores each set on
+// the same samples); kept out of SampleParams, whose size the hot kernels are sensitive to.
+struct ExtraBlocked {
+    const int32_t* v;
+    uint32_t n;
 };
 
 // Whether v is one of the sample's extra blocked vertices (a handful at most).
-__device__ __forceinline__ bool extra_blocked(const SampleParams& P, uint32_t v)
+__device__ __forceinline__ bool extra_blocked(const ExtraBlocked& x, uint32_t v)
 {
-    for (uint32_t i = 0; i < P.n_extra; ++i)
-        if (static_cast<uint32_t>(P.extra[i]) == v) return true;
+    for (uint32_t i = 0; i < x.n; ++i)
+        if (static_cast<uint32_t>(x.v[i]) == v) return true;
     return false;
 }
 

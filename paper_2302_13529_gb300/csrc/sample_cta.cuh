@@ -84,7 +84,7 @@ template <bool kSpread>
 __device__ __forceinline__ void visit_staged(const SampleParams& P, const CtaCfg& C, uint32_t* bm,
                                              CtaShared& sh, const Slot& S, const uint2* stage,
                                              uint32_t count, uint32_t lane,
-                                             unsigned long long& lv)
+                                             unsigned long long& lv, const ExtraBlocked& xb)
 {
     for (uint32_t s0 = 0; s0 < count; s0 += 32) {
         const bool act = s0 + lane < count;
@@ -96,7 +96,7 @@ __device__ __forceinline__ void visit_staged(const SampleParams& P, const CtaCfg
             ul = c.x;
             v = static_cast<uint32_t>(__ldg(P.g.col + c.y));
             row = make_int2(__ldg(P.g.row_ptr + v), __ldg(P.g.row_ptr + v + 1));
-            if (!excluded(P.excl, v) && !(kSpread && extra_blocked(P, v))) {
+            if (!excluded(P.excl, v) && !(kSpread && extra_blocked(xb, v))) {
                 ++lv;
                 const uint32_t bit = 1u << (v & 31);
                 disc = (atomicOr(bm + (v >> 5), bit) & bit) == 0;
@@ -274,12 +274,14 @@ __device__ __forceinline__ bool finish_tree_packed(const SampleParams& P, CtaSha
 // bm: visited bitmap (shared or global memory); res: 2 * C.res_slots words of shared memory for
 // the non-tree target resolution -- the bitmap itself when kResInBitmap (it is cleared first).
 // kSpread: only the BFS; |R| (seeds included) is added to sc.reached and the dominator step is
-// skipped (the Monte-Carlo spread estimate of Def. 3).
+// skipped (the Monte-Carlo spread estimate of Def. 3); xb lists vertices blocked in this sample
+// only (reachability mode).
 template <bool kResInBitmap, bool kSpread = false, int M = kModelAny>
 __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCfg& C, uint32_t* bm,
                                               uint32_t* res, CtaShared& sh, const Slot& S, uint32_t j,
                                               uint32_t tid, SampleCounters& sc,
-                                              unsigned long long& examined, unsigned long long& live)
+                                              unsigned long long& examined, unsigned long long& live,
+                                              ExtraBlocked xb = ExtraBlocked{nullptr, 0u})
 {
     const uint32_t ns = P.ns;
     const uint32_t lane = tid & 31, wid = tid >> 5;
@@ -389,14 +391,14 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
                 staged += __shfl_sync(kFull, cincl, 31);
                 if (staged > kStage - 32 * 4) {  // the next iteration could overflow the stage
                     __syncwarp();
-                    visit_staged<kSpread>(P, C, bm, sh, S, sh.stage[wid], staged, lane, lv);
+                    visit_staged<kSpread>(P, C, bm, sh, S, sh.stage[wid], staged, lane, lv, xb);
                     __syncwarp();
                     staged = 0;
                 }
             }
             if (staged > 0) {
                 __syncwarp();
-                visit_staged<kSpread>(P, C, bm, sh, S, sh.stage[wid], staged, lane, lv);
+                visit_staged<kSpread>(P, C, bm, sh, S, sh.stage[wid], staged, lane, lv, xb);
                 __syncwarp();
             }
             __syncthreads();

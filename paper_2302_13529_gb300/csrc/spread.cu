@@ -100,11 +100,9 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_spread_sets(SampleParams P, 
         if (item >= items) break;
         const uint32_t set = static_cast<uint32_t>(item / P.theta);
         const uint32_t j = static_cast<uint32_t>(item % P.theta);
-        SampleParams Q = P;
-        Q.extra = sets + static_cast<uint64_t>(set) * k;
-        Q.n_extra = k;
         const unsigned long long before = sc.reached;
-        const int rc = run_sample_cta<kSmemBitmap, true>(Q, C, bm, dsm, sh, S, j, tid, sc, examined, live);
+        const int rc = run_sample_cta<kSmemBitmap, true>(P, C, bm, dsm, sh, S, j, tid, sc, examined, live,
+                                                         ExtraBlocked{sets + static_cast<uint64_t>(set) * k, k});
         if (tid == 0) {
             if (rc != kSampleDone) atomicOr(&P.ctl->error, rc == kSampleOverflow ? kErrCapacity : kErrInternal);
             else atomicAdd(sums + set, sc.reached - before);
