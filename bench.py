@@ -375,6 +375,7 @@ def leg_batch(steps: int, warmup: int, key_offset: int = 0) -> dict:
     hs = [imin.load_graph(q.graph) for q in qs]
     items = [(h, q.seeds, q.b, q.theta, q.key + key_offset) for h, q in zip(hs, qs)]
     samples = sum(q.b * q.theta for q in qs)  # every query runs b rounds (n - |S| >= b here)
+    chunk = imin.autotune_batch(items, 0)  # queue granularity, tuned outside the timing
     for _ in range(max(warmup, 1)):
         imin.batch_advanced_greedy(items)
     torch.cuda.synchronize()
@@ -410,7 +411,8 @@ def leg_batch(steps: int, warmup: int, key_offset: int = 0) -> dict:
             "theta": 20000, "samples_per_call": samples,
             "total_edges": int(sum(q.graph.m for q in qs)), "generation_s": round(gen_s, 1),
             "batched": {"value": samples / batched_s, "unit": "samples/s", "seconds": batched_s,
-                        "calls": steps, "gpu_launches_per_call": launches / max(steps, 1)},
+                        "calls": steps, "gpu_launches_per_call": launches / max(steps, 1),
+                        "samples_per_work_item": chunk},
             "one_query_per_launch": {"value": samples / plain_s, "unit": "samples/s",
                                      "seconds": plain_s, "cutoff": "autotuned per graph before timing"},
             "batched_over_plain": plain_s / batched_s, "bit_exact_vs_plain": same,

@@ -249,6 +249,19 @@ int imin_batch_advanced_greedy(imin_query* queries, int32_t n_queries, void* str
 /* Alg. 4 for every query of `queries`; GreedyReplace's phase-2 early stop is per query. */
 int imin_batch_greedy_replace(imin_query* queries, int32_t n_queries, void* stream);
 
+/* Pick the queue granularity of a batch (samples of one query per work item of a step; the
+ * paper has no counterpart) and keep it for the life of the process under a fingerprint of the
+ * batch (per query: its graph's fingerprint, seed-set size, budget and theta; and the driver).
+ * After a warm-up call, times the first 3 steps of the batch for each candidate {4, 8, 16, 32,
+ * 64}, twice, and keeps the fastest; later imin_batch_* calls on the same batch use it (others use
+ * min(16, theta-dependent default)). The granularity never changes a result. The tuning calls
+ * write into scratch buffers: the queries' outputs are not touched.
+ *   driver     0 = AdvancedGreedy, 1 = GreedyReplace
+ *   out_chunk  receives the chosen granularity
+ * Synchronizes `stream`. Errors as for imin_batch_advanced_greedy. */
+int imin_autotune_batch(imin_query* queries, int32_t n_queries, int32_t driver, void* stream,
+                        int32_t* out_chunk);
+
 /* ---- serving: continuous batching of queries --------------------------------------------
  * A server owns a worker thread and a CUDA stream on the current device. Requests (an
  * AdvancedGreedy or GreedyReplace query on a loaded graph) are admitted in arrival order

@@ -7,6 +7,7 @@
 // stream-ordered allocator and are released on the same stream.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
@@ -932,7 +933,32 @@ int greedy_impl(Driver which, const imin_graph* g, const int32_t* seeds, int32_t
 
 // ---- batched drivers ------------------------------------------------------------------------
 
-int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
+// Queue granularity (samples per work item) of batched steps, picked by imin_autotune_batch and
+// kept for the life of the process under a fingerprint of the batch: the driver and, per query,
+// its graph's fingerprint, seed-set size, budget and theta.
+std::mutex g_chunk_mu;
+std::map<uint64_t, uint32_t> g_batch_chunk;
+
+uint64_t batch_fingerprint(Driver which, const imin_query* qs, int32_t nq)
+{
+    uint64_t h = which == Driver::kGreedyReplace ? 0x9e3779b97f4a7c15ull : 0x7f4a7c159e3779b9ull;
+    auto mix = [&](uint64_t x) {
+        h ^= x + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+        h *= 0x100000001b3ull;
+    };
+    for (int32_t i = 0; i < nq; ++i) {
+        mix(qs[i].graph ? qs[i].graph->fingerprint : 0);
+        mix((static_cast<uint64_t>(static_cast<uint32_t>(qs[i].n_seeds)) << 32) | static_cast<uint32_t>(qs[i].b));
+        mix(qs[i].theta);
+    }
+    return h;
+}
+
+// force_chunk: samples per work item (0: the tuned value of this batch, else the default rule);
+// max_steps: stop after that many steps (< 0: run to the end; used by the tuner, whose outputs
+// are then partial).
+int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream, uint32_t force_chunk = 0,
+               int32_t max_steps = -1)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (nq < 0 || (nq > 0 && qs == nullptr)) return fail(IMIN_ERR_INVALID, "queries array is NULL");
@@ -1095,6 +1121,7 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
         d.done = warp_q[i] ? buf + off[i].done : nullptr;
         steps = std::max(steps, gr ? 2 * count[i] : count[i]);
     }
+    if (max_steps >= 0) steps = std::min(steps, max_steps);
     IMIN_CUDA(cudaMemcpyAsync(dq, hq.data(), sizeof(BatchQuery) * nq, cudaMemcpyHostToDevice, s));
 
     // per-step item prefixes: one row per size class (queries of other classes and inactive
@@ -1105,6 +1132,13 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream)
     uint32_t chunk = static_cast<uint32_t>(std::max<uint64_t>(
         1, std::min<uint64_t>(16, sum_theta / (static_cast<uint64_t>(cta_blocks[0] + cta_blocks[1] +
                                                                      cta_blocks[2] + cta_blocks[3]) * 16 + 1))));
+    if (force_chunk > 0) {
+        chunk = force_chunk;
+    } else {
+        std::lock_guard<std::mutex> lk(g_chunk_mu);
+        const auto it = g_batch_chunk.find(batch_fingerprint(which, qs, nq));
+        if (it != g_batch_chunk.end()) chunk = it->second;
+    }
     if (const char* v = std::getenv("IMIN_BATCH_CHUNK"); v && *v)
         chunk = std::max<uint32_t>(1, static_cast<uint32_t>(std::strtoul(v, nullptr, 10)));
     constexpr int kRows = kBatchClasses + 1;
@@ -1412,6 +1446,49 @@ int imin_autotune(const imin_graph* g, const int32_t* seeds, int32_t n_seeds, ui
         g_tuned[{g->fingerprint, size_class(hseeds.size())}] = static_cast<int32_t>(c);
     }
     *out_cutoff = static_cast<int32_t>(c);
+    return IMIN_OK;
+}
+
+int imin_autotune_batch(imin_query* queries, int32_t n_queries, int32_t driver, void* stream,
+                        int32_t* out_chunk)
+{
+    g_err[0] = '\0';
+    if (out_chunk == nullptr) return fail(IMIN_ERR_INVALID, "out_chunk is NULL");
+    if (driver != 0 && driver != 1) return fail(IMIN_ERR_INVALID, "driver must be 0 (AG) or 1 (GR)");
+    if (n_queries < 0 || (n_queries > 0 && queries == nullptr)) return fail(IMIN_ERR_INVALID, "queries array is NULL");
+    *out_chunk = 0;
+    if (n_queries == 0) return IMIN_OK;
+    const Driver which = driver == 1 ? Driver::kGreedyReplace : Driver::kAdvancedGreedy;
+    // the tuning calls write into scratch outputs, never into the caller's
+    std::vector<imin_query> q(queries, queries + n_queries);
+    std::vector<std::vector<int32_t>> outs(static_cast<size_t>(n_queries));
+    for (int32_t i = 0; i < n_queries; ++i) {
+        outs[i].assign(static_cast<size_t>(std::max(q[i].b, 1)), 0);
+        q[i].out_blockers = outs[i].data();
+    }
+    constexpr uint32_t kChunks[] = {4, 8, 16, 32, 64};
+    constexpr int32_t kTuneSteps = 3;
+    int rc = batch_impl(which, q.data(), n_queries, stream, 16, kTuneSteps);  // warm-up, cutoff tuning
+    if (rc) return rc;
+    double best_s = 0;
+    uint32_t best = 16;
+    for (int rep = 0; rep < 2; ++rep) {
+        for (uint32_t c : kChunks) {
+            const auto t0 = std::chrono::steady_clock::now();
+            rc = batch_impl(which, q.data(), n_queries, stream, c, kTuneSteps);
+            if (rc) return rc;
+            const double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if ((rep == 0 && c == kChunks[0]) || s < best_s) {
+                best_s = s;
+                best = c;
+            }
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_chunk_mu);
+        g_batch_chunk[batch_fingerprint(which, queries, n_queries)] = best;
+    }
+    *out_chunk = static_cast<int32_t>(best);
     return IMIN_OK;
 }
 

@@ -106,6 +106,8 @@ def lib():
         L.imin_random_blockers.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, P, P]
         for name in ("imin_batch_advanced_greedy", "imin_batch_greedy_replace"):
             getattr(L, name).argtypes = [ctypes.POINTER(Query), ctypes.c_int32, P]
+        L.imin_autotune_batch.argtypes = [ctypes.POINTER(Query), ctypes.c_int32, ctypes.c_int32, P,
+                                          ctypes.POINTER(ctypes.c_int32)]
         L.imin_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
         L.imin_server_submit.argtypes = [P, ctypes.c_int32, P, P, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_uint32, ctypes.c_uint64,
@@ -311,8 +313,7 @@ def random_blockers(gh: GraphHandle, seeds, b, key):
     return out[:cnt.value]
 
 
-def _batch(fn, items, stream):
-    """items: sequence of (GraphHandle, seeds, b, theta, key[, out]) -> list of blocker arrays."""
+def _queries(items):
     arr = (Query * max(len(items), 1))()
     keep, outs = [], []
     for i, it in enumerate(items):
@@ -324,8 +325,22 @@ def _batch(fn, items, stream):
         outs.append(out)
         arr[i] = Query(gh.handle.value, s.value if s is not None else None, ns, int(b), int(theta),
                        int(key), o.value, 0)
+    return arr, keep, outs
+
+
+def _batch(fn, items, stream):
+    """items: sequence of (GraphHandle, seeds, b, theta, key[, out]) -> list of blocker arrays."""
+    arr, keep, outs = _queries(items)
     _check(fn(arr, len(items), _stream(stream)))
     return [outs[i][:arr[i].out_count] for i in range(len(items))]
+
+
+def autotune_batch(items, driver=0, stream=None) -> int:
+    """imin_autotune_batch: pick and cache the queue granularity of this batch; returns it."""
+    arr, keep, outs = _queries(items)
+    c = ctypes.c_int32()
+    _check(lib().imin_autotune_batch(arr, len(items), int(driver), _stream(stream), ctypes.byref(c)))
+    return c.value
 
 
 def batch_advanced_greedy(items, stream=None):

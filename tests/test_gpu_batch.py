@@ -99,3 +99,21 @@ def test_batch_warp_block_cutoff(cuda_lib, monkeypatch, cutoff):
             assert st["tier_samples"][0] == 0
         else:
             assert st["tier_samples"][0] > 0 and st["tier_samples"][3] > 0, st
+
+
+def test_batch_queue_granularity_tuning(cuda_lib, monkeypatch):
+    """imin_autotune_batch picks one of its candidates, leaves the callers' outputs alone, and the
+    batch keeps giving the single-query results with the tuned and with forced granularities."""
+    qs = _queries(8, seed=31)
+    hs = [cuda_lib.load_graph(q[0]) for q in qs]
+    outs = [np.full(max(b, 1), -7, np.int32) for (g, s, b, t, k) in qs]
+    items = [(hh, s, b, t, k, o) for hh, (g, s, b, t, k), o in zip(hs, qs, outs)]
+    c = cuda_lib.autotune_batch(items, 1)
+    assert c in (4, 8, 16, 32, 64)
+    assert all((o == -7).all() for o in outs)
+    want = [cuda_lib.greedy_replace(*it[:5]) for it in items]
+    for forced in (None, "1", "3", "1000"):
+        if forced:
+            monkeypatch.setenv("IMIN_BATCH_CHUNK", forced)
+        got = cuda_lib.batch_greedy_replace([it[:5] for it in items])
+        assert all(np.array_equal(a, b) for a, b in zip(got, want)), forced
