@@ -213,7 +213,7 @@ def profile_fields(kernel: str, workload: str = WORKLOAD) -> dict:
     out = {}
     for line in open(path):
         k, sep, v = line.partition(":")
-        if sep and k and all(c.islower() or c == "_" for c in k):
+        if sep and k and k[0].islower() and all(c.islower() or c.isdigit() or c == "_" for c in k):
             out[k] = v.strip()
     return out
 
@@ -264,8 +264,11 @@ def roofline_of(prof: dict, stats: dict, n_seeds: int, workload: str = WORKLOAD)
            "avg_launch_ms": avg_ms, "launches": kp["launches"],
            "share_of_device_time": kp["ms"] / max(total, 1e-9),
            "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
-    if "issue_active_pct" in fields and fields.get("source_hash") == kernel_source_hash():
-        out["issue_active_pct"] = float(fields["issue_active_pct"])
+    if fields.get("source_hash") == kernel_source_hash():
+        # the other ncu figures of the same capture (issue-slot use, L2 throughput and hit rate,
+        # warp execution efficiency, L2 -> SM bytes per launch)
+        out["ncu"] = {k: float(v) for k, v in fields.items()
+                      if k not in ("source_hash", "dram_bytes_per_launch")}
     return out
 
 

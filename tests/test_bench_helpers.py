@@ -56,6 +56,32 @@ def test_traffic_only_for_the_sources_it_was_measured_on(tmp_path, monkeypatch):
     assert bench.ncu_traffic("k_other") is None  # no summary at all
 
 
+def test_ncu_figures_follow_the_source_hash(tmp_path, monkeypatch):
+    """The summary's other header figures reach roofline.ncu, and the bound turns to "issue",
+    only while the summary was taken on the current kernel sources."""
+    prof_dir = tmp_path / "profiles"
+    prof_dir.mkdir()
+    csrc = tmp_path / "paper_2302_13529_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES:
+        (csrc / f).write_text(f"// {f} v1\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.kernel_source_hash()
+    (prof_dir / f"k_sample_cta_{bench.WORKLOAD}.md").write_text(
+        f"# x\nsource_hash: {h}\ndram_bytes_per_launch: 100\nissue_active_pct: 58.5\n"
+        "l2_hit_rate_pct: 87.6\n")
+    prof = {k: {"launches": 0, "ms": 0.0} for k in ("sample_tier0", "sample_tier1", "sample_tier2",
+                                                     "sample_cta", "select", "other")}
+    prof["sample_cta"] = {"launches": 2, "ms": 4.0}
+    st = _stats(reached=1000, examined=100000, live=900, samples=10)
+    r = bench.roofline_of(prof, st, 3)
+    assert r["bound"] == "issue" and r["traffic"] == 100.0
+    assert r["ncu"] == {"issue_active_pct": 58.5, "l2_hit_rate_pct": 87.6}
+    (csrc / bench.KERNEL_SOURCES[0]).write_text("// changed\n")
+    r = bench.roofline_of(prof, st, 3)
+    assert r["bound"] == "hbm" and r["traffic"] is None and "ncu" not in r
+
+
 def test_committed_profile_names_its_kernel_sources():
     """The committed block-tier summary carries a source hash and a traffic figure."""
     path = os.path.join(bench.ROOT, "profiles", f"k_sample_cta_{bench.WORKLOAD}.md")
