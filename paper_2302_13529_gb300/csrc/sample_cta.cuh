@@ -41,12 +41,22 @@ constexpr uint32_t kStage = 192;                    // live edges staged per war
                                                     // another full iteration might not fit)
 constexpr uint32_t kCtaLevels = 512;
 
+// 16-bit tree entries that fit in the BFS arrays below once the BFS is over
+constexpr uint32_t kTree16 = (8 * kCtaWarps * kStage + 12 * kChunk) / 2;
+
 struct CtaShared {
-    uint32_t incl[kChunk];  // inclusive group count of the chunk's vertices
-    int32_t beg[kChunk];    // their edge ranges
-    int32_t end[kChunk];
+    union {
+        struct {
+            uint2 stage[kCtaWarps][kStage];  // (local id of the source, edge id)
+            uint32_t incl[kChunk];           // inclusive group count of the chunk's vertices
+            int32_t beg[kChunk];             // their edge ranges
+            int32_t end[kChunk];
+        } b;
+        // the dominator passes of large trees: immediate dominators of local ids past the
+        // resolution space, as 16-bit entries
+        uint16_t tree16[kTree16];
+    };
     uint32_t lvl[kCtaLevels + 1];
-    uint2 stage[kCtaWarps][kStage];  // (local id of the source, edge id)
     uint32_t wsum[kCtaWarps];
     uint32_t item, nR, nE, flag;
 };
@@ -195,25 +205,81 @@ __device__ __forceinline__ bool finish_tree(const SampleParams& P, CtaShared& sh
     return broken;
 }
 
-// finish_tree with the first K local ids -- the shallowest BFS levels, which every NCA walk ends
-// in -- held as one shared-memory word per vertex, (idom << 16) | c, and ids K..nR-1 (kSplit) in
-// the slot arrays (idom in S.idom; c in S.par, which is dead once the passes end). For trees of
-// fewer than 2^16 vertices: c is 0 in the shared words during the dominator passes, so atomicMin
-// on the whole word is atomicMin on idom, and in the sweep c < 2^16 never carries into idom.
-template <bool kSplit>
-__device__ __forceinline__ bool finish_tree_packed(const SampleParams& P, CtaShared& sh, const Slot& S,
-                                                   uint32_t* w, uint32_t K, uint32_t nR, uint32_t nE,
-                                                   uint32_t nlev, uint32_t ns, uint32_t tid,
-                                                   uint32_t* passes_out)
+// The dominator passes of finish_tree on packed shared-memory words, one per local id,
+// (idom << 16) | c with c = 0 (every id fits: nR <= K), so atomicMin on the word is atomicMin on
+// idom.
+__device__ __forceinline__ bool tree_passes_packed(const Slot& S, uint32_t* w, uint32_t nR, uint32_t nE,
+                                                   uint32_t tid, uint32_t* passes_out)
 {
     volatile uint32_t* vw = w;
+    bool broken = false;
+    uint32_t passes = 0;
+    if (nE > 0) {
+        for (;;) {
+            int changed = 0;
+            for (uint32_t k = tid; k < nE; k += kCtaThreads) {
+                const uint2 e = S.edges[k];
+                uint32_t a = vw[e.y] >> 16, b = e.x;
+                for (uint32_t g = 0; a != b; ++g) {
+                    if (g > 2 * nR) { broken = true; a = 0; break; }
+                    if (a > b) a = vw[a] >> 16;
+                    else b = vw[b] >> 16;
+                }
+                b = S.par[e.y];
+                for (uint32_t g = 0; a != b; ++g) {
+                    if (g > 2 * nR) { broken = true; a = 0; break; }
+                    if (a > b) a = vw[a] >> 16;
+                    else b = vw[b] >> 16;
+                }
+                if (!broken && a < (vw[e.y] >> 16)) {
+                    const uint32_t old = atomicMin(w + e.y, a << 16);
+                    changed |= (a << 16) < old;
+                }
+            }
+            ++passes;
+            broken = __syncthreads_or(broken);
+            if (broken || !__syncthreads_or(changed)) break;
+            if (passes > nR + 1) { broken = true; break; }
+        }
+    }
+    *passes_out = passes;
+    return broken;
+}
+
+// Lower a 16-bit shared entry to min(entry, a) (compare-and-swap on its 32-bit word); 1 if it
+// fell, 0 if not, -1 if the swap kept failing (cannot happen: each failure means another thread
+// lowered a neighbouring or the same entry, and entries only fall).
+__device__ __forceinline__ int lower16(uint16_t* p, uint32_t a)
+{
+    uint32_t* w = reinterpret_cast<uint32_t*>(reinterpret_cast<uintptr_t>(p) & ~static_cast<uintptr_t>(3));
+    const uint32_t sh = (reinterpret_cast<uintptr_t>(p) & 2) ? 16u : 0u;
+    uint32_t old = *reinterpret_cast<volatile uint32_t*>(w);
+    for (uint32_t it = 0; it < (1u << 20); ++it) {
+        if (a >= ((old >> sh) & 0xFFFFu)) return 0;
+        const uint32_t prev = atomicCAS(w, old, (old & ~(0xFFFFu << sh)) | (a << sh));
+        if (prev == old) return 1;
+        old = prev;
+    }
+    return -1;
+}
+
+// The dominator passes of finish_tree for trees of fewer than 2^16 vertices that outgrow the
+// packed words: idom as 16-bit shared entries for local ids below KA (the resolution space, 16
+// bits per id) and KA .. KA + kTree16 - 1 (the BFS arrays, free once the BFS is over), the
+// deepest ids in S.idom. Every NCA walk climbs to smaller ids, so almost all of its steps are
+// shared-memory loads. On return S.idom holds the final immediate dominators of all ids.
+__device__ __forceinline__ bool tree_passes16(CtaShared& sh, const Slot& S, uint16_t* a16, uint32_t KA,
+                                              uint32_t nR, uint32_t nE, uint32_t tid, uint32_t* passes_out)
+{
+    uint16_t* b16 = sh.tree16;
+    const uint32_t na = min(nR, KA), nb = min(nR, KA + kTree16);
+    for (uint32_t i = tid; i < na; i += kCtaThreads) a16[i] = static_cast<uint16_t>(ld_tree(S.idom + i));
+    for (uint32_t i = KA + tid; i < nb; i += kCtaThreads) b16[i - KA] = static_cast<uint16_t>(ld_tree(S.idom + i));
+    __syncthreads();
     auto idom_of = [&](uint32_t x) -> uint32_t {
-        if (!kSplit || x < K) return vw[x] >> 16;
-        return __ldcg(S.idom + x);
-    };
-    auto c_of = [&](uint32_t x) -> uint32_t {
-        if (!kSplit || x < K) return vw[x] & 0xFFFFu;
-        return __ldcg(S.par + x);
+        if (x < KA) return *reinterpret_cast<volatile uint16_t*>(a16 + x);
+        if (x < KA + kTree16) return *reinterpret_cast<volatile uint16_t*>(b16 + (x - KA));
+        return ld_tree(S.idom + x);
     };
     bool broken = false;
     uint32_t passes = 0;
@@ -235,13 +301,12 @@ __device__ __forceinline__ bool finish_tree_packed(const SampleParams& P, CtaSha
                     else b = idom_of(b);
                 }
                 if (!broken && a < idom_of(e.y)) {
-                    if (!kSplit || e.y < K) {
-                        const uint32_t old = atomicMin(w + e.y, a << 16);
-                        changed |= (a << 16) < old;
-                    } else {
-                        const uint32_t old = atomicMin(S.idom + e.y, a);
-                        changed |= a < old;
-                    }
+                    int fell;
+                    if (e.y < KA) fell = lower16(a16 + e.y, a);
+                    else if (e.y < KA + kTree16) fell = lower16(b16 + (e.y - KA), a);
+                    else fell = a < atomicMin(S.idom + e.y, a) ? 1 : 0;
+                    if (fell < 0) broken = true;
+                    changed |= fell > 0;
                 }
             }
             ++passes;
@@ -251,6 +316,31 @@ __device__ __forceinline__ bool finish_tree_packed(const SampleParams& P, CtaSha
         }
     }
     *passes_out = passes;
+    for (uint32_t i = tid; i < na; i += kCtaThreads) S.idom[i] = a16[i];
+    for (uint32_t i = KA + tid; i < nb; i += kCtaThreads) S.idom[i] = b16[i - KA];
+    __syncthreads();
+    return broken;
+}
+
+// Subtree sizes (deepest level first) and Delta += c for reached non-seeds, once the immediate
+// dominators are final, with the first K local ids -- the shallowest BFS levels -- as packed
+// shared-memory words (idom << 16) | c and ids K..nR-1 (kSplit) on the slot arrays (idom in
+// S.idom; c in S.par, which is dead once the passes end). For trees of fewer than 2^16
+// vertices: c < 2^16 never carries into idom. On entry w[i] = idom(i) << 16 for i < K.
+template <bool kSplit>
+__device__ __forceinline__ void tree_sweep_packed(const SampleParams& P, CtaShared& sh, const Slot& S,
+                                                  uint32_t* w, uint32_t K, uint32_t nR, uint32_t nlev,
+                                                  uint32_t ns, uint32_t tid)
+{
+    volatile uint32_t* vw = w;
+    auto idom_of = [&](uint32_t x) -> uint32_t {
+        if (!kSplit || x < K) return vw[x] >> 16;
+        return __ldcg(S.idom + x);
+    };
+    auto c_of = [&](uint32_t x) -> uint32_t {
+        if (!kSplit || x < K) return vw[x] & 0xFFFFu;
+        return __ldcg(S.par + x);
+    };
     for (uint32_t i = tid; i < K; i += kCtaThreads) w[i] = (vw[i] & 0xFFFF0000u) | 1u;
     if constexpr (kSplit) {
         for (uint32_t i = K + tid; i < nR; i += kCtaThreads) S.par[i] = 1;
@@ -268,7 +358,6 @@ __device__ __forceinline__ bool finish_tree_packed(const SampleParams& P, CtaSha
     for (uint32_t i = 1 + ns + tid; i < nR; i += kCtaThreads)
         atomicAdd(P.delta + S.gid[i], static_cast<unsigned long long>(c_of(i)));
     __syncthreads();
-    return broken;
 }
 
 // bm: visited bitmap (shared or global memory); res: 2 * C.res_slots words of shared memory for
@@ -334,9 +423,9 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
 #pragma unroll
             for (uint32_t k = 0; k < kVpt; ++k) {
                 run += ng[k];
-                sh.incl[tid * kVpt + k] = run;
-                sh.beg[tid * kVpt + k] = beg[k];
-                sh.end[tid * kVpt + k] = end[k];
+                sh.b.incl[tid * kVpt + k] = run;
+                sh.b.beg[tid * kVpt + k] = beg[k];
+                sh.b.end[tid * kVpt + k] = end[k];
             }
             if (lane == 31) sh.wsum[wid] = wincl;
             __syncthreads();
@@ -363,10 +452,10 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
                     uint32_t p = w * (kVpt * 32);
 #pragma unroll
                     for (uint32_t step = kVpt * 16; step >= 1; step >>= 1)
-                        if (sh.incl[p + step - 1] <= tl) p += step;
-                    nob = sh.beg[p];
-                    noe = sh.end[p];
-                    const uint32_t first = (p & (kVpt * 32 - 1)) ? sh.incl[p - 1] : 0u;
+                        if (sh.b.incl[p + step - 1] <= tl) p += step;
+                    nob = sh.b.beg[p];
+                    noe = sh.b.end[p];
+                    const uint32_t first = (p & (kVpt * 32 - 1)) ? sh.b.incl[p - 1] : 0u;
                     nq = (static_cast<uint32_t>(nob) >> 2) + (tl - first);
                     nul = base + p;
                     nth = __ldg(P.g.thr4 + nq);
@@ -386,19 +475,19 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
                 while (m) {
                     const uint32_t i = __ffs(m) - 1;
                     m &= m - 1;
-                    sh.stage[wid][w++] = make_uint2(ul, (q << 2) + i);
+                    sh.b.stage[wid][w++] = make_uint2(ul, (q << 2) + i);
                 }
                 staged += __shfl_sync(kFull, cincl, 31);
                 if (staged > kStage - 32 * 4) {  // the next iteration could overflow the stage
                     __syncwarp();
-                    visit_staged<kSpread>(P, C, bm, sh, S, sh.stage[wid], staged, lane, lv, xb);
+                    visit_staged<kSpread>(P, C, bm, sh, S, sh.b.stage[wid], staged, lane, lv, xb);
                     __syncwarp();
                     staged = 0;
                 }
             }
             if (staged > 0) {
                 __syncwarp();
-                visit_staged<kSpread>(P, C, bm, sh, S, sh.stage[wid], staged, lane, lv, xb);
+                visit_staged<kSpread>(P, C, bm, sh, S, sh.b.stage[wid], staged, lane, lv, xb);
                 __syncwarp();
             }
             __syncthreads();
@@ -468,16 +557,26 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
         if (broken) return kSampleError;
     }
 
-    // dominators, subtree sizes and counter update: the shallowest ids that fit the (now free)
-    // resolution space as packed shared-memory words, the rest on the slot arrays; trees of 2^16
-    // vertices or more entirely on the slot arrays
+    // dominators, subtree sizes and counter update: trees that fit the (now free) resolution
+    // space as packed shared-memory words entirely there; larger trees of fewer than 2^16
+    // vertices with 16-bit immediate dominators in shared memory for the passes and the
+    // shallowest ids packed for the sweep, the rest on the slot arrays; trees of 2^16 vertices
+    // or more entirely on the slot arrays
     uint32_t passes = 0;
     if (nR < (1u << 16)) {
         const uint32_t K = min(nR, C.tree_words);
-        for (uint32_t i = tid; i < K; i += kCtaThreads) res[i] = S.idom[i] << 16;
-        __syncthreads();
-        broken = K == nR ? finish_tree_packed<false>(P, sh, S, res, K, nR, nE, nlev, ns, tid, &passes)
-                         : finish_tree_packed<true>(P, sh, S, res, K, nR, nE, nlev, ns, tid, &passes);
+        if (K == nR) {
+            for (uint32_t i = tid; i < K; i += kCtaThreads) res[i] = S.idom[i] << 16;
+            __syncthreads();
+            broken = tree_passes_packed(S, res, nR, nE, tid, &passes);
+            tree_sweep_packed<false>(P, sh, S, res, K, nR, nlev, ns, tid);
+        } else {
+            broken = tree_passes16(sh, S, reinterpret_cast<uint16_t*>(res), 2 * C.tree_words, nR, nE, tid,
+                                   &passes);
+            for (uint32_t i = tid; i < K; i += kCtaThreads) res[i] = ld_tree(S.idom + i) << 16;
+            __syncthreads();
+            tree_sweep_packed<true>(P, sh, S, res, K, nR, nlev, ns, tid);
+        }
         if constexpr (kResInBitmap) {
             for (uint32_t i = tid; i < K; i += kCtaThreads) res[i] = 0;  // it is the bitmap
             __syncthreads();
