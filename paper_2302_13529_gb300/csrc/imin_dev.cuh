@@ -291,6 +291,20 @@ struct WarpSpace {
 
 // Loads of words that other lanes update with atomics or stores during the same sample.
 // Global scratch is read through L2 (.cg) so that no stale L1 line is ever used.
+
+// One step of the two-finger NCA walk over immediate dominators: the finger with the larger local
+// id (the deeper one; ids follow BFS discovery order, so a dominator's id is smaller) moves to its
+// immediate dominator. Written with selects, so every lane of a warp issues exactly one load per
+// step whichever finger it moves.
+template <typename F>
+__device__ __forceinline__ void nca_step(uint32_t& a, uint32_t& b, F idom_of)
+{
+    const bool up_a = a > b;
+    const uint32_t nx = idom_of(up_a ? a : b);
+    a = up_a ? nx : a;
+    b = up_a ? b : nx;
+}
+
 template <bool G>
 __device__ __forceinline__ uint32_t ld_shared_word(const uint32_t* p)
 {
@@ -518,14 +532,12 @@ __device__ __forceinline__ int run_sample(const SampleParams& P, const WarpSpace
                 // both chains strictly decrease towards the super-seed (id 0)
                 for (uint32_t guard = 0; a != b; ++guard) {
                     if (guard > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = ld_shared_word<G>(w.idom + a);
-                    else b = ld_shared_word<G>(w.idom + b);
+                    nca_step(a, b, [&](uint32_t x) { return ld_shared_word<G>(w.idom + x); });
                 }
                 b = w.par[e.y];
                 for (uint32_t guard = 0; a != b; ++guard) {
                     if (guard > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = ld_shared_word<G>(w.idom + a);
-                    else b = ld_shared_word<G>(w.idom + b);
+                    nca_step(a, b, [&](uint32_t x) { return ld_shared_word<G>(w.idom + x); });
                 }
                 if (!broken && a < ld_shared_word<G>(w.idom + e.y)) {
                     const uint32_t old = atomicMin(w.idom + e.y, a);

@@ -171,14 +171,12 @@ __device__ __forceinline__ bool finish_tree(const SampleParams& P, CtaShared& sh
                 uint32_t a = ld_tree(idom + e.y), b = e.x;
                 for (uint32_t g = 0; a != b; ++g) {
                     if (g > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = ld_tree(idom + a);
-                    else b = ld_tree(idom + b);
+                    nca_step(a, b, [&](uint32_t x) { return ld_tree(idom + x); });
                 }
                 b = S.par[e.y];
                 for (uint32_t g = 0; a != b; ++g) {
                     if (g > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = ld_tree(idom + a);
-                    else b = ld_tree(idom + b);
+                    nca_step(a, b, [&](uint32_t x) { return ld_tree(idom + x); });
                 }
                 if (!broken && a < ld_tree(idom + e.y)) {
                     const uint32_t old = atomicMin(idom + e.y, a);
@@ -222,14 +220,12 @@ __device__ __forceinline__ bool tree_passes_packed(const Slot& S, uint32_t* w, u
                 uint32_t a = vw[e.y] >> 16, b = e.x;
                 for (uint32_t g = 0; a != b; ++g) {
                     if (g > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = vw[a] >> 16;
-                    else b = vw[b] >> 16;
+                    nca_step(a, b, [&](uint32_t x) { return vw[x] >> 16; });
                 }
                 b = S.par[e.y];
                 for (uint32_t g = 0; a != b; ++g) {
                     if (g > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = vw[a] >> 16;
-                    else b = vw[b] >> 16;
+                    nca_step(a, b, [&](uint32_t x) { return vw[x] >> 16; });
                 }
                 if (!broken && a < (vw[e.y] >> 16)) {
                     const uint32_t old = atomicMin(w + e.y, a << 16);
@@ -244,6 +240,14 @@ __device__ __forceinline__ bool tree_passes_packed(const Slot& S, uint32_t* w, u
     }
     *passes_out = passes;
     return broken;
+}
+
+// Volatile 16-bit shared-memory load at a shared-space byte address.
+__device__ __forceinline__ uint32_t lds_u16(uint32_t addr)
+{
+    unsigned short v;
+    asm volatile("ld.volatile.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr) : "memory");
+    return v;
 }
 
 // Lower a 16-bit shared entry to min(entry, a) (compare-and-swap on its 32-bit word); 1 if it
@@ -276,9 +280,11 @@ __device__ __forceinline__ bool tree_passes16(CtaShared& sh, const Slot& S, uint
     for (uint32_t i = tid; i < na; i += kCtaThreads) a16[i] = static_cast<uint16_t>(ld_tree(S.idom + i));
     for (uint32_t i = KA + tid; i < nb; i += kCtaThreads) b16[i - KA] = static_cast<uint16_t>(ld_tree(S.idom + i));
     __syncthreads();
+    // one shared-memory load for either region (an address select, no branch)
+    const uint32_t base_a = static_cast<uint32_t>(__cvta_generic_to_shared(a16));
+    const uint32_t base_b = static_cast<uint32_t>(__cvta_generic_to_shared(b16));
     auto idom_of = [&](uint32_t x) -> uint32_t {
-        if (x < KA) return *reinterpret_cast<volatile uint16_t*>(a16 + x);
-        if (x < KA + kTree16) return *reinterpret_cast<volatile uint16_t*>(b16 + (x - KA));
+        if (x < KA + kTree16) return lds_u16(x < KA ? base_a + 2 * x : base_b + 2 * (x - KA));
         return ld_tree(S.idom + x);
     };
     bool broken = false;
@@ -291,14 +297,12 @@ __device__ __forceinline__ bool tree_passes16(CtaShared& sh, const Slot& S, uint
                 uint32_t a = idom_of(e.y), b = e.x;
                 for (uint32_t g = 0; a != b; ++g) {
                     if (g > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = idom_of(a);
-                    else b = idom_of(b);
+                    nca_step(a, b, idom_of);
                 }
                 b = S.par[e.y];
                 for (uint32_t g = 0; a != b; ++g) {
                     if (g > 2 * nR) { broken = true; a = 0; break; }
-                    if (a > b) a = idom_of(a);
-                    else b = idom_of(b);
+                    nca_step(a, b, idom_of);
                 }
                 if (!broken && a < idom_of(e.y)) {
                     int fell;
