@@ -80,10 +80,11 @@ __device__ __forceinline__ SampleParams params_of(const BatchQuery& Q, uint32_t 
 }
 
 template <bool kSmemBitmap, int M>
-__global__ void __launch_bounds__(kCtaThreads, 8) k_batch_cta(BatchStep B, CtaCfg C)
+__global__ void __launch_bounds__(cta_threads<kSmemBitmap>(), 1024 / cta_threads<kSmemBitmap>()) k_batch_cta(BatchStep B, CtaCfg C)
 {
+    constexpr uint32_t kCtaThreads = cta_threads<kSmemBitmap>();
     extern __shared__ __align__(16) uint32_t dsm[];
-    __shared__ CtaShared sh;
+    __shared__ CtaShared<kCtaThreads> sh;
     __shared__ unsigned long long s_item;
     __shared__ uint32_t s_q;
     __shared__ int s_skip;
@@ -328,12 +329,12 @@ bool plan_batch_cta(const DeviceInfo& dev, int32_t max_n, int32_t max_m, CtaCfg*
         if (allow_max_dynamic_smem(k_batch_cta<false, kModelIC>, dev) != cudaSuccess ||
             allow_max_dynamic_smem(k_batch_cta<false, kModelAny>, dev) != cudaSuccess)
             return false;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta<false, kModelIC>, kCtaThreads, *smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta<false, kModelIC>, cta_threads<false>(), *smem);
     } else {
         if (allow_max_dynamic_smem(k_batch_cta<true, kModelIC>, dev) != cudaSuccess ||
             allow_max_dynamic_smem(k_batch_cta<true, kModelAny>, dev) != cudaSuccess)
             return false;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta<true, kModelIC>, kCtaThreads, *smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta<true, kModelIC>, cta_threads<true>(), *smem);
     }
     if (occ <= 0) return false;
     *blocks = static_cast<uint32_t>(occ) * dev.sms;
@@ -378,11 +379,11 @@ cudaError_t launch_batch_cta(const BatchStep& B, const CtaCfg& c, uint32_t block
     CtaCfg cfg = c;
     cfg.scratch = scratch;
     if (c.global_bitmap) {
-        if (B.all_ic) k_batch_cta<false, kModelIC><<<blocks, kCtaThreads, smem, s>>>(B, cfg);
-        else k_batch_cta<false, kModelAny><<<blocks, kCtaThreads, smem, s>>>(B, cfg);
+        if (B.all_ic) k_batch_cta<false, kModelIC><<<blocks, cta_threads<false>(), smem, s>>>(B, cfg);
+        else k_batch_cta<false, kModelAny><<<blocks, cta_threads<false>(), smem, s>>>(B, cfg);
     } else {
-        if (B.all_ic) k_batch_cta<true, kModelIC><<<blocks, kCtaThreads, smem, s>>>(B, cfg);
-        else k_batch_cta<true, kModelAny><<<blocks, kCtaThreads, smem, s>>>(B, cfg);
+        if (B.all_ic) k_batch_cta<true, kModelIC><<<blocks, cta_threads<true>(), smem, s>>>(B, cfg);
+        else k_batch_cta<true, kModelAny><<<blocks, cta_threads<true>(), smem, s>>>(B, cfg);
     }
     return cudaGetLastError();
 }

@@ -1,5 +1,5 @@
 // sample_cta.cu -- single-query launch of the block-per-sample tier of Alg. 2 (the routine is
-// in sample_cta.cuh): a persistent grid of 128-thread blocks takes samples from an atomic cursor
+// in sample_cta.cuh): a persistent grid of blocks takes samples from an atomic cursor
 // -- all of [0, theta), or the samples the warp tier 0 handed over when it ran first -- and a
 // sample the block tier cannot hold is handed to the whole-graph warp tier.
 #include <algorithm>
@@ -19,10 +19,11 @@ using namespace cta;
 // resolution hash; otherwise it lives in the block's global slot and the dynamic shared memory
 // holds only the resolution hash.
 template <bool kSmemBitmap, int M>
-__global__ void __launch_bounds__(kCtaThreads, 8) k_sample_cta(SampleParams P, CtaCfg C)
+__global__ void __launch_bounds__(cta_threads<kSmemBitmap>(), 1024 / cta_threads<kSmemBitmap>()) k_sample_cta(SampleParams P, CtaCfg C)
 {
+    constexpr uint32_t kCtaThreads = cta_threads<kSmemBitmap>();
     extern __shared__ __align__(16) uint32_t dsm[];
-    __shared__ CtaShared sh;
+    __shared__ CtaShared<kCtaThreads> sh;
     const uint32_t tid = threadIdx.x;
     if (P.done != nullptr && *reinterpret_cast<const volatile int32_t*>(P.done) != 0) return;
 
@@ -133,11 +134,11 @@ bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint3
     if (smem_bitmap) {
         allow_max_dynamic_smem(k_sample_cta<true, kModelLT>, dev);
         allow_max_dynamic_smem(k_sample_cta<true, kModelIC>, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta<true, kModelIC>, kCtaThreads, *smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta<true, kModelIC>, cta_threads<true>(), *smem);
     } else {
         allow_max_dynamic_smem(k_sample_cta<false, kModelLT>, dev);
         allow_max_dynamic_smem(k_sample_cta<false, kModelIC>, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta<false, kModelIC>, kCtaThreads, *smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sample_cta<false, kModelIC>, cta_threads<false>(), *smem);
     }
     if (occ <= 0) return false;
     *blocks = static_cast<uint32_t>(occ) * dev.sms;
@@ -159,11 +160,11 @@ cudaError_t launch_cta_tier(const SampleParams& P, const CtaCfg& c, uint32_t blo
     cfg.scratch = scratch;
     const bool lt = P.g.lo4 != nullptr;
     if (c.global_bitmap) {
-        if (lt) k_sample_cta<false, kModelLT><<<blocks, kCtaThreads, smem, s>>>(P, cfg);
-        else k_sample_cta<false, kModelIC><<<blocks, kCtaThreads, smem, s>>>(P, cfg);
+        if (lt) k_sample_cta<false, kModelLT><<<blocks, cta_threads<false>(), smem, s>>>(P, cfg);
+        else k_sample_cta<false, kModelIC><<<blocks, cta_threads<false>(), smem, s>>>(P, cfg);
     } else {
-        if (lt) k_sample_cta<true, kModelLT><<<blocks, kCtaThreads, smem, s>>>(P, cfg);
-        else k_sample_cta<true, kModelIC><<<blocks, kCtaThreads, smem, s>>>(P, cfg);
+        if (lt) k_sample_cta<true, kModelLT><<<blocks, cta_threads<true>(), smem, s>>>(P, cfg);
+        else k_sample_cta<true, kModelIC><<<blocks, cta_threads<true>(), smem, s>>>(P, cfg);
     }
     return cudaGetLastError();
 }

@@ -1,12 +1,14 @@
-// sample_cta.cuh -- the block-per-sample routine of Alg. 2 for graphs whose visited bitmap fits
-// in shared memory (n <= 2^18), shared by the single-query kernel (sample_cta.cu) and the
-// batched multi-query kernel (batch.cu).
+// sample_cta.cuh -- the block-per-sample routine of Alg. 2, shared by the single-query kernel
+// (sample_cta.cu), the batched multi-query kernel (batch.cu) and the spread estimate (spread.cu).
+// The visited bitmap is in shared memory for graphs of up to 2^18 vertices and in the block's
+// global slot for larger ones.
 //
-// One 128-thread block owns one sampled graph at a time (persistent over the samples of the
-// call through an atomic cursor):
+// One block owns one sampled graph at a time (persistent over the samples of the call through
+// an atomic cursor); it has 128 threads when the visited bitmap is in shared memory and 256 when
+// it is in global memory (cta_threads below):
 //   * visited set: an n-bit bitmap in shared memory; discovering a vertex is one shared-memory
 //     atomicOr, so no cascade size ever overflows the visited structure;
-//   * BFS level by level, 256 frontier vertices per block-wide scan: their out-edges are
+//   * BFS level by level, 2 frontier vertices per thread per block-wide scan: their out-edges are
 //     flattened into 4-edge groups; each thread takes one group per iteration (binary search
 //     for the owner row), loads its 4 thresholds with one 16-byte load and decides them with
 //     one Philox4x32-10 call;
@@ -33,31 +35,47 @@
 namespace imin {
 namespace cta {
 
-constexpr uint32_t kCtaThreads = 128;
-constexpr uint32_t kCtaWarps = kCtaThreads / 32;
-constexpr uint32_t kVpt = 2;                        // frontier vertices per thread per chunk
-constexpr uint32_t kChunk = kCtaThreads * kVpt;     // frontier vertices per chunk
-constexpr uint32_t kStage = 192;                    // live edges staged per warp (visited once
-                                                    // another full iteration might not fit)
+constexpr uint32_t kVpt = 2;        // frontier vertices per thread per chunk
+constexpr uint32_t kStage = 192;    // live edges staged per warp (visited once another full
+                                    // iteration might not fit)
 constexpr uint32_t kCtaLevels = 512;
 
-// 16-bit tree entries that fit in the BFS arrays below once the BFS is over
-constexpr uint32_t kTree16 = (8 * kCtaWarps * kStage + 12 * kChunk) / 2;
+// Threads per block. With the visited bitmap in shared memory (n <= 2^18) a block has 128
+// threads, and 8 blocks share an SM. With the bitmap in global memory (larger graphs, whose
+// cascades are larger and bound by memory latency) a block has kCtaThreadsGlobal threads, so a
+// cascade gets more threads and fewer cascades share an SM.
+constexpr uint32_t kCtaThreadsSmem = 128;
+constexpr uint32_t kCtaThreadsGlobal = 256;
+template <bool kSmemBitmap>
+__host__ __device__ constexpr uint32_t cta_threads()
+{
+    return kSmemBitmap ? kCtaThreadsSmem : kCtaThreadsGlobal;
+}
 
+template <uint32_t T>
+struct CtaDims {
+    static_assert(T % 32 == 0 && T <= 1024, "whole warps");
+    static constexpr uint32_t kWarps = T / 32;
+    static constexpr uint32_t kChunk = T * kVpt;  // frontier vertices per chunk
+    // 16-bit tree entries that fit in the BFS arrays of CtaShared once the BFS is over
+    static constexpr uint32_t kTree16 = (8 * kWarps * kStage + 12 * kChunk) / 2;
+};
+
+template <uint32_t T>
 struct CtaShared {
     union {
         struct {
-            uint2 stage[kCtaWarps][kStage];  // (local id of the source, edge id)
-            uint32_t incl[kChunk];           // inclusive group count of the chunk's vertices
-            int32_t beg[kChunk];             // their edge ranges
-            int32_t end[kChunk];
+            uint2 stage[CtaDims<T>::kWarps][kStage];  // (local id of the source, edge id)
+            uint32_t incl[CtaDims<T>::kChunk];        // inclusive group count of the chunk's vertices
+            int32_t beg[CtaDims<T>::kChunk];          // their edge ranges
+            int32_t end[CtaDims<T>::kChunk];
         } b;
         // the dominator passes of large trees: immediate dominators of local ids past the
         // resolution space, as 16-bit entries
-        uint16_t tree16[kTree16];
+        uint16_t tree16[CtaDims<T>::kTree16];
     };
     uint32_t lvl[kCtaLevels + 1];
-    uint32_t wsum[kCtaWarps];
+    uint32_t wsum[CtaDims<T>::kWarps];
     uint32_t item, nR, nE, flag;
 };
 
@@ -90,9 +108,9 @@ struct Slot {
 // Visit the staged live edges of one warp: test-and-set the visited bit of each target; a new
 // vertex gets the next local id (one shared atomic per warp), an old one yields a non-tree edge.
 // kSpread: reachability only -- no parents, dominator seeds or non-tree edges are recorded.
-template <bool kSpread>
+template <bool kSpread, uint32_t T>
 __device__ __forceinline__ void visit_staged(const SampleParams& P, const CtaCfg& C, uint32_t* bm,
-                                             CtaShared& sh, const Slot& S, const uint2* stage,
+                                             CtaShared<T>& sh, const Slot& S, const uint2* stage,
                                              uint32_t count, uint32_t lane,
                                              unsigned long long& lv, const ExtraBlocked& xb)
 {
@@ -157,10 +175,12 @@ __device__ __forceinline__ uint32_t ld_tree(const uint32_t* p) { return __ldcg(p
 // non-seeds, on the slot arrays in global memory, for trees too large for shared memory (c
 // reuses the parent array, which is dead once the passes end). Returns true when the iteration
 // failed its bounds (cannot happen for a well-formed sample).
-__device__ __forceinline__ bool finish_tree(const SampleParams& P, CtaShared& sh, const Slot& S,
+template <uint32_t T>
+__device__ __forceinline__ bool finish_tree(const SampleParams& P, CtaShared<T>& sh, const Slot& S,
                                             uint32_t* idom, uint32_t* c, uint32_t nR, uint32_t nE,
                                             uint32_t nlev, uint32_t ns, uint32_t tid, uint32_t* passes_out)
 {
+    constexpr uint32_t kCtaThreads = T;
     bool broken = false;
     uint32_t passes = 0;
     if (nE > 0) {
@@ -206,9 +226,11 @@ __device__ __forceinline__ bool finish_tree(const SampleParams& P, CtaShared& sh
 // The dominator passes of finish_tree on packed shared-memory words, one per local id,
 // (idom << 16) | c with c = 0 (every id fits: nR <= K), so atomicMin on the word is atomicMin on
 // idom.
+template <uint32_t T>
 __device__ __forceinline__ bool tree_passes_packed(const Slot& S, uint32_t* w, uint32_t nR, uint32_t nE,
                                                    uint32_t tid, uint32_t* passes_out)
 {
+    constexpr uint32_t kCtaThreads = T;
     volatile uint32_t* vw = w;
     bool broken = false;
     uint32_t passes = 0;
@@ -272,9 +294,11 @@ __device__ __forceinline__ int lower16(uint16_t* p, uint32_t a)
 // bits per id) and KA .. KA + kTree16 - 1 (the BFS arrays, free once the BFS is over), the
 // deepest ids in S.idom. Every NCA walk climbs to smaller ids, so almost all of its steps are
 // shared-memory loads. On return S.idom holds the final immediate dominators of all ids.
-__device__ __forceinline__ bool tree_passes16(CtaShared& sh, const Slot& S, uint16_t* a16, uint32_t KA,
+template <uint32_t T>
+__device__ __forceinline__ bool tree_passes16(CtaShared<T>& sh, const Slot& S, uint16_t* a16, uint32_t KA,
                                               uint32_t nR, uint32_t nE, uint32_t tid, uint32_t* passes_out)
 {
+    constexpr uint32_t kCtaThreads = T, kTree16 = CtaDims<T>::kTree16;
     uint16_t* b16 = sh.tree16;
     const uint32_t na = min(nR, KA), nb = min(nR, KA + kTree16);
     for (uint32_t i = tid; i < na; i += kCtaThreads) a16[i] = static_cast<uint16_t>(ld_tree(S.idom + i));
@@ -331,11 +355,12 @@ __device__ __forceinline__ bool tree_passes16(CtaShared& sh, const Slot& S, uint
 // shared-memory words (idom << 16) | c and ids K..nR-1 (kSplit) on the slot arrays (idom in
 // S.idom; c in S.par, which is dead once the passes end). For trees of fewer than 2^16
 // vertices: c < 2^16 never carries into idom. On entry w[i] = idom(i) << 16 for i < K.
-template <bool kSplit>
-__device__ __forceinline__ void tree_sweep_packed(const SampleParams& P, CtaShared& sh, const Slot& S,
+template <bool kSplit, uint32_t T>
+__device__ __forceinline__ void tree_sweep_packed(const SampleParams& P, CtaShared<T>& sh, const Slot& S,
                                                   uint32_t* w, uint32_t K, uint32_t nR, uint32_t nlev,
                                                   uint32_t ns, uint32_t tid)
 {
+    constexpr uint32_t kCtaThreads = T;
     volatile uint32_t* vw = w;
     auto idom_of = [&](uint32_t x) -> uint32_t {
         if (!kSplit || x < K) return vw[x] >> 16;
@@ -369,13 +394,14 @@ __device__ __forceinline__ void tree_sweep_packed(const SampleParams& P, CtaShar
 // kSpread: only the BFS; |R| (seeds included) is added to sc.reached and the dominator step is
 // skipped (the Monte-Carlo spread estimate of Def. 3); xb lists vertices blocked in this sample
 // only (reachability mode).
-template <bool kResInBitmap, bool kSpread = false, int M = kModelAny>
+template <bool kResInBitmap, bool kSpread = false, int M = kModelAny, uint32_t T>
 __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCfg& C, uint32_t* bm,
-                                              uint32_t* res, CtaShared& sh, const Slot& S, uint32_t j,
+                                              uint32_t* res, CtaShared<T>& sh, const Slot& S, uint32_t j,
                                               uint32_t tid, SampleCounters& sc,
                                               unsigned long long& examined, unsigned long long& live,
                                               ExtraBlocked xb = ExtraBlocked{nullptr, 0u})
 {
+    constexpr uint32_t kCtaThreads = T, kCtaWarps = CtaDims<T>::kWarps, kChunk = CtaDims<T>::kChunk;
     const uint32_t ns = P.ns;
     const uint32_t lane = tid & 31, wid = tid >> 5;
     for (uint32_t i = tid; i < ns; i += kCtaThreads) {
@@ -433,9 +459,16 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
             }
             if (lane == 31) sh.wsum[wid] = wincl;
             __syncthreads();
-            static_assert(kCtaWarps == 4, "the warp offsets below assume 4 warps");
-            const uint32_t off1 = sh.wsum[0], off2 = off1 + sh.wsum[1], off3 = off2 + sh.wsum[2];
-            const uint32_t total = off3 + sh.wsum[3];
+            uint32_t woff[kCtaWarps];  // inclusive warp totals
+            {
+                uint32_t run = 0;
+#pragma unroll
+                for (uint32_t k = 0; k < kCtaWarps; ++k) {
+                    run += sh.wsum[k];
+                    woff[k] = run;
+                }
+            }
+            const uint32_t total = woff[kCtaWarps - 1];
 
             // ---- groups: one per thread per iteration; live edges accumulate in the warp's
             // stage, which is visited by the full warp whenever it is at least half full and
@@ -451,8 +484,14 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
                 noe = 0;
                 if (t < total) {
                     // the owner's warp, then the owner within the warp's kVpt * 32 entries
-                    const uint32_t w = (t >= off1 ? 1u : 0u) + (t >= off2 ? 1u : 0u) + (t >= off3 ? 1u : 0u);
-                    const uint32_t tl = t - (w == 0 ? 0u : w == 1 ? off1 : w == 2 ? off2 : off3);
+                    uint32_t w = 0, wb = 0;
+#pragma unroll
+                    for (uint32_t k = 0; k + 1 < kCtaWarps; ++k) {
+                        const bool past = t >= woff[k];
+                        w = past ? k + 1 : w;
+                        wb = past ? woff[k] : wb;
+                    }
+                    const uint32_t tl = t - wb;
                     uint32_t p = w * (kVpt * 32);
 #pragma unroll
                     for (uint32_t step = kVpt * 16; step >= 1; step >>= 1)
@@ -572,7 +611,7 @@ __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCf
         if (K == nR) {
             for (uint32_t i = tid; i < K; i += kCtaThreads) res[i] = S.idom[i] << 16;
             __syncthreads();
-            broken = tree_passes_packed(S, res, nR, nE, tid, &passes);
+            broken = tree_passes_packed<T>(S, res, nR, nE, tid, &passes);
             tree_sweep_packed<false>(P, sh, S, res, K, nR, nlev, ns, tid);
         } else {
             broken = tree_passes16(sh, S, reinterpret_cast<uint16_t*>(res), 2 * C.tree_words, nR, nE, tid,

@@ -14,11 +14,12 @@ namespace {
 using namespace cta;
 
 template <bool kSmemBitmap>
-__global__ void __launch_bounds__(kCtaThreads, 8) k_spread_cta(SampleParams P, CtaCfg C,
+__global__ void __launch_bounds__(cta_threads<kSmemBitmap>(), 1024 / cta_threads<kSmemBitmap>()) k_spread_cta(SampleParams P, CtaCfg C,
                                                                unsigned long long* sum)
 {
+    constexpr uint32_t kCtaThreads = cta_threads<kSmemBitmap>();
     extern __shared__ __align__(16) uint32_t dsm[];
-    __shared__ CtaShared sh;
+    __shared__ CtaShared<kCtaThreads> sh;
     const uint32_t tid = threadIdx.x;
     uint8_t* base = C.scratch + static_cast<uint64_t>(blockIdx.x) * C.slot_bytes;
     Slot S;
@@ -70,13 +71,14 @@ __global__ void __launch_bounds__(kCtaThreads, 8) k_spread_cta(SampleParams P, C
 // sample runs with the set's k vertices blocked on top of excl, and its |R| (seeds included) is
 // added to sums[set]. Every set sees the same samples (common random numbers).
 template <bool kSmemBitmap>
-__global__ void __launch_bounds__(kCtaThreads, 8) k_spread_sets(SampleParams P, CtaCfg C, const int32_t* sets,
+__global__ void __launch_bounds__(cta_threads<kSmemBitmap>(), 1024 / cta_threads<kSmemBitmap>()) k_spread_sets(SampleParams P, CtaCfg C, const int32_t* sets,
                                                                 uint32_t k, unsigned long long items,
                                                                 unsigned long long* cursor,
                                                                 unsigned long long* sums)
 {
+    constexpr uint32_t kCtaThreads = cta_threads<kSmemBitmap>();
     extern __shared__ __align__(16) uint32_t dsm[];
-    __shared__ CtaShared sh;
+    __shared__ CtaShared<kCtaThreads> sh;
     __shared__ unsigned long long s_item;
     const uint32_t tid = threadIdx.x;
     uint8_t* base = C.scratch + static_cast<uint64_t>(blockIdx.x) * C.slot_bytes;
@@ -122,10 +124,10 @@ cudaError_t launch_spread_sets(const SampleParams& P, const CtaCfg& c, uint32_t 
     const DeviceInfo dev = device_info();
     if (c.global_bitmap) {
         allow_max_dynamic_smem(k_spread_sets<false>, dev);
-        k_spread_sets<false><<<blocks, kCtaThreads, smem, s>>>(P, cfg, sets, k, items, cursor, sums);
+        k_spread_sets<false><<<blocks, cta_threads<false>(), smem, s>>>(P, cfg, sets, k, items, cursor, sums);
     } else {
         allow_max_dynamic_smem(k_spread_sets<true>, dev);
-        k_spread_sets<true><<<blocks, kCtaThreads, smem, s>>>(P, cfg, sets, k, items, cursor, sums);
+        k_spread_sets<true><<<blocks, cta_threads<true>(), smem, s>>>(P, cfg, sets, k, items, cursor, sums);
     }
     return cudaGetLastError();
 }
@@ -139,10 +141,10 @@ cudaError_t launch_spread(const SampleParams& P, const CtaCfg& c, uint32_t block
     const DeviceInfo dev = device_info();
     if (c.global_bitmap) {
         allow_max_dynamic_smem(k_spread_cta<false>, dev);
-        k_spread_cta<false><<<blocks, kCtaThreads, smem, s>>>(P, cfg, sum);
+        k_spread_cta<false><<<blocks, cta_threads<false>(), smem, s>>>(P, cfg, sum);
     } else {
         allow_max_dynamic_smem(k_spread_cta<true>, dev);
-        k_spread_cta<true><<<blocks, kCtaThreads, smem, s>>>(P, cfg, sum);
+        k_spread_cta<true><<<blocks, cta_threads<true>(), smem, s>>>(P, cfg, sum);
     }
     return cudaGetLastError();
 }
