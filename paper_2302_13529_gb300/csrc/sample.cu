@@ -166,7 +166,7 @@ TierPlan plan_tiers(const DeviceInfo& dev, int32_t n, int32_t m, uint32_t ns, ui
     if (allow_cta && plan_cta_tier(dev, n, m, &p.cta, &p.blocks[kTierCta], &p.smem_bytes[kTierCta],
                                    &p.scratch_bytes[kTierCta])) {
         p.use_cta = true;
-        p.warps_per_block[kTierCta] = 4;
+        p.warps_per_block[kTierCta] = p.cta.global_bitmap ? 8u : 4u;  // 256- or 128-thread blocks
         // tier 2 only catches the rare samples with too many non-tree edges or levels
         t2_budget = std::min<uint64_t>(t2_budget, 1ull << 30);
         r0 = cutoff;
