@@ -470,7 +470,7 @@ def leg_rmat22(b=None, theta=None, key_offset: int = 0) -> dict:
                      "tier_samples": st["tier_samples"]}}
 
 
-def leg_serving(requests: int, seed: int = 5000) -> dict:
+def leg_serving(requests: int, seed: int = 5000, max_class_samples: int = 0) -> dict:
     """Requests against the R-MAT 2^17 (m=2^20) and R-MAT 2^22 (m=2^26) WC graphs held resident:
     each picks a graph with probability 1/2, |S| ~ U[10, 500], b ~ U[10, 100],
     theta ~ U[1e4, 1e5] (AdvancedGreedy).
@@ -495,7 +495,7 @@ def leg_serving(requests: int, seed: int = 5000) -> dict:
 
     def serve(arrivals):
         lat = [None] * len(reqs)
-        with imin.Server() as srv:
+        with imin.Server(max_class_samples=max_class_samples) as srv:
             t0 = time.perf_counter()
             tickets = [None] * len(reqs)
 

@@ -264,12 +264,16 @@ int imin_autotune_batch(imin_query* queries, int32_t n_queries, int32_t driver, 
 
 /* ---- serving: continuous batching of queries --------------------------------------------
  * A server owns a worker thread and a CUDA stream on the current device. Requests (an
- * AdvancedGreedy or GreedyReplace query on a loaded graph) are admitted in arrival order
- * whenever a batch slot is free and their device state (about 8n + n/4 bytes plus seeds and
- * blockers) fits the memory budget. Every step advances all admitted requests by one greedy
- * round in shared launches (one Alg. 2 launch per graph-size class over the sampled graphs of
- * every admitted request, then one selection launch); a request admitted at step t runs its own
- * rounds 0, 1, ... at steps t, t+1, ..., so its random stream and result are exactly those of
+ * AdvancedGreedy or GreedyReplace query on a loaded graph) are admitted in arrival order within
+ * their graph-size class whenever a batch slot is free, their device state (about 8n + n/4
+ * bytes plus seeds and blockers) fits the memory budget and their class is under its per-step
+ * sample cap (more requests of one class per step add little throughput once their samples fill
+ * the GPU, and every one of them would finish later). Each step advances the admitted requests of one graph-size
+ * class (n <= 2^16, 2^17, 2^18, larger) by one greedy round in shared launches (one Alg. 2 launch
+ * over the sampled graphs of those requests, then one selection launch). The class a step
+ * serves is the busy class that has had the least GPU time, so requests on small graphs advance
+ * at their own pace next to requests on large ones. A request runs its own rounds 0, 1, ... on
+ * the steps that serve its class, so its random stream and result are exactly those of
  * imin_advanced_greedy / imin_greedy_replace called alone. Finished requests leave between
  * steps and free their slot and memory. Graphs must stay loaded until their requests finish.
  * At admission each request takes its graph's tuned warp/block cutoff (tuned on the server's
@@ -279,7 +283,10 @@ typedef struct imin_server imin_server;
 typedef struct imin_server_config {
     uint64_t memory_budget;  /* bytes of request state the server may hold (0: 1/4 of free memory) */
     int32_t max_active;      /* batch slots (0: 256) */
-    int32_t reserved;
+    int32_t max_class_samples;  /* sampled graphs per step that one size class may batch across its
+                                   requests (0: 200,000). A pending request waits while its class
+                                   is at the cap (it runs alone when it exceeds the cap by itself);
+                                   pending requests of other classes are admitted past it. */
 } imin_server_config;
 
 typedef struct imin_server_stats {

@@ -1,9 +1,13 @@
 // server.cu -- continuous-batching request server for AdvancedGreedy / GreedyReplace queries.
 //
-// A worker thread owns one CUDA stream and runs steps. Each step advances every admitted
-// request by one greedy round through the batched kernels (batch.cu): one block-per-sample
-// launch per graph-size class over the samples of all admitted requests, the whole-graph
-// fallback, and one selection launch with a block per request slot. Requests are admitted
+// A worker thread owns one CUDA stream and runs steps. Each step advances the admitted requests
+// of one graph-size class by one greedy round through the batched kernels (batch.cu): the
+// block-per-sample launch over their samples, the whole-graph fallback, and one selection launch
+// with a block per request slot. The class a step serves is the one with the least GPU time so
+// far among the classes with requests (a class that becomes busy joins at the smallest time of
+// the busy ones), so requests on small graphs are not held to the pace of the large graphs'
+// rounds; a request that sits a step out keeps its round count (its start step moves with the
+// step counter). Requests are admitted
 // between steps, in arrival order, while a slot is free and their device state (counters,
 // masks, seeds, blockers) fits the memory budget; a request joins at the current step, so its
 // own round index is step - start and its random stream is exactly the one the single-query
@@ -77,6 +81,7 @@ void plan_request(Req& r, uint32_t cutoff)
 struct imin_server {
     uint64_t budget = 0;
     int32_t max_active = 0;
+    uint64_t class_cap = 0;  // sampled graphs per step one size class may batch
     int device = 0;
     DeviceInfo dev;
     cudaStream_t s = nullptr;
@@ -126,7 +131,11 @@ struct imin_server {
     uint32_t warp_blocks = 0;
     uint64_t warp_smem = 0;
     uint32_t step = 0;
+    // GPU time each size class has had (milliseconds of its steps) and which classes were busy
+    double class_ms[kBatchClasses] = {};
+    bool class_was_busy[kBatchClasses] = {};
 
+    int choose_class(const std::vector<Req*>& active);
     void run();
     int grow_plans(const std::vector<Req*>& active);
     void finish(Req* r, int status);
@@ -230,6 +239,22 @@ int imin_server::grow_plans(const std::vector<Req*>& active)
     return IMIN_OK;
 }
 
+int imin_server::choose_class(const std::vector<Req*>& active)
+{
+    bool busy[kBatchClasses] = {};
+    for (Req* r : active) busy[batch_class(r->g->n)] = true;
+    double floor_ms = -1.0;
+    for (int k = 0; k < kBatchClasses; ++k)
+        if (busy[k] && class_was_busy[k] && (floor_ms < 0 || class_ms[k] < floor_ms)) floor_ms = class_ms[k];
+    int best = -1;
+    for (int k = 0; k < kBatchClasses; ++k) {
+        if (busy[k] && !class_was_busy[k] && floor_ms >= 0) class_ms[k] = std::max(class_ms[k], floor_ms);
+        class_was_busy[k] = busy[k];
+        if (busy[k] && (best < 0 || class_ms[k] < class_ms[best])) best = k;
+    }
+    return best;
+}
+
 void imin_server::run()
 {
     cudaSetDevice(device);
@@ -239,9 +264,19 @@ void imin_server::run()
         {
             std::unique_lock<std::mutex> lk(mu);
             for (;;) {
-                // admission: arrival order, while a slot is free and the state fits the budget
-                while (!pending.empty()) {
-                    Req* r = pending.front();
+                // admission: arrival order within a size class, while a slot is free, the state
+                // fits the budget and the class's samples per step stay under the cap (a class
+                // at its cap is passed over, not waited for)
+                uint64_t class_samples[kBatchClasses] = {};
+                for (Req* r : slots)
+                    if (r != nullptr) class_samples[batch_class(r->g->n)] += r->theta;
+                for (auto it = pending.begin(); it != pending.end();) {
+                    Req* r = *it;
+                    const int k = batch_class(r->g->n);
+                    if (class_samples[k] > 0 && class_samples[k] + r->theta > class_cap) {
+                        ++it;
+                        continue;
+                    }
                     int free_slot = -1;
                     for (int i = 0; i < max_active; ++i)
                         if (slots[i] == nullptr) {
@@ -249,10 +284,11 @@ void imin_server::run()
                             break;
                         }
                     if (free_slot < 0 || (used + r->bytes > budget && used > 0)) break;
-                    pending.pop_front();
+                    it = pending.erase(it);
                     r->slot = free_slot;
                     slots[free_slot] = r;
                     used += r->bytes;
+                    class_samples[k] += r->theta;
                     admitted.push_back(r);
                     st.admitted += 1;
                 }
@@ -303,10 +339,13 @@ void imin_server::run()
             if (r->count <= 0) finished_now.push_back(r);
         }
 
-        // the active set of this step and its descriptors
+        // the active set, the class this step serves, and the descriptors (a request of another
+        // class is uploaded with a start beyond this step, which the kernels treat as inactive)
         std::vector<Req*> active;
         for (Req* r : slots)
             if (r != nullptr && r->count > 0) active.push_back(r);
+        const int serve = choose_class(active);
+        auto served = [serve](const Req* r) { return batch_class(r->g->n) == serve; };
         {
             const int rc = grow_plans(active);
             if (rc != IMIN_OK) {
@@ -330,10 +369,10 @@ void imin_server::run()
             d.blockers = reinterpret_cast<int32_t*>(r->mem + r->off_blk);
             d.count = r->count;
             d.flags = dflags + 2 * r->slot;
-            d.start = r->start;
+            d.start = served(r) ? r->start : step + 1;
             d.gr = r->driver == kGR ? 1 : 0;
             d.done = r->warp && warp_ok ? r->mem + r->off_done : nullptr;
-            sum_theta += r->theta;
+            if (served(r)) sum_theta += r->theta;
         }
         if (sum_theta > over_cap) {
             if (dover) cudaFreeAsync(dover, s);
@@ -353,7 +392,7 @@ void imin_server::run()
                 const Req* r = slots[i];
                 const bool in_row = r != nullptr && (k < kBatchClasses ? batch_class(r->g->n) == k
                                                                         : r->warp && warp_ok);
-                const bool act = in_row && r->count > 0;
+                const bool act = in_row && r->count > 0 && served(r);
                 pr[i + 1] = pr[i] + (act ? (r->theta + chunk - 1) / chunk : 0);
             }
             class_busy[k] = pr[max_active] > 0;
@@ -364,6 +403,7 @@ void imin_server::run()
             SRV_CUDA(cudaMemcpyAsync(dq, hq, sizeof(BatchQuery) * max_active, cudaMemcpyHostToDevice, s));
             SRV_CUDA(cudaMemcpyAsync(dprefix, hprefix, sizeof(unsigned long long) * kPrefixRows * stride,
                                      cudaMemcpyHostToDevice, s));
+            const Clock::time_point t_step = Clock::now();
             SRV_CUDA(cudaMemsetAsync(dctl, 0, sizeof(BatchCtl), s));
             BatchStep B{};
             B.q = dq;
@@ -376,7 +416,8 @@ void imin_server::run()
             B.stats = nullptr;
             B.prefix = dprefix;
             B.all_ic = 1;
-            for (Req* r : active) B.all_ic = B.all_ic && r->g->model == 0 ? 1u : 0u;
+            for (Req* r : active)
+                if (served(r)) B.all_ic = B.all_ic && r->g->model == 0 ? 1u : 0u;
             // every slot follows its own driver's schedule (BatchQuery::gr)
             if (any_gr) SRV_CUDA(launch_batch_unblock(B, s));
             if (class_busy[kBatchClasses]) {
@@ -401,7 +442,12 @@ void imin_server::run()
                          "a batched step reported a kernel error");
                 return;
             }
+            class_ms[serve] += std::chrono::duration<double, std::milli>(Clock::now() - t_step).count();
             for (Req* r : active) {
+                if (!served(r)) {
+                    r->start += 1;  // sat this step out: its next round is still step + 1 - start
+                    continue;
+                }
                 const int32_t rr = static_cast<int32_t>(step - r->start);
                 const bool last = r->driver == kAG ? rr + 1 >= r->count
                                                    : (hflags[2 * r->slot] != 0 || rr + 1 >= 2 * r->count);
@@ -447,6 +493,7 @@ int imin_server_create(const imin_server_config* cfg, imin_server** out)
     cudaMemGetInfo(&free_b, &total_b);
     srv->budget = (cfg && cfg->memory_budget) ? cfg->memory_budget : static_cast<uint64_t>(free_b / 4);
     srv->max_active = (cfg && cfg->max_active > 0) ? cfg->max_active : 256;
+    srv->class_cap = (cfg && cfg->max_class_samples > 0) ? static_cast<uint64_t>(cfg->max_class_samples) : 200000u;
     srv->cutoff = 0;
     srv->slots.assign(srv->max_active, nullptr);
     const size_t stride = static_cast<size_t>(srv->max_active) + 1;

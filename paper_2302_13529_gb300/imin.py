@@ -57,7 +57,7 @@ class Query(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("memory_budget", ctypes.c_uint64), ("max_active", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("max_class_samples", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -355,14 +355,15 @@ def batch_greedy_replace(items, stream=None):
 
 class Server:
     """Continuous-batching request server (imin_server_*): submit queries at any time; each is
-    admitted when a batch slot and its device memory are available, advanced one greedy round per
-    shared step with all other admitted requests, and returns exactly the result of running it
-    alone."""
+    admitted when a batch slot, its device memory and room under its size class's per-step sample
+    cap are available, advanced one greedy round per shared step with the other admitted requests
+    of its size class (the classes take turns by GPU time), and returns exactly the result of
+    running it alone."""
 
     AG, GR = 0, 1
 
-    def __init__(self, memory_budget: int = 0, max_active: int = 0):
-        cfg = ServerConfig(int(memory_budget), int(max_active), 0)
+    def __init__(self, memory_budget: int = 0, max_active: int = 0, max_class_samples: int = 0):
+        cfg = ServerConfig(int(memory_budget), int(max_active), int(max_class_samples))
         h = ctypes.c_void_p()
         _check(lib().imin_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

@@ -103,3 +103,37 @@ def test_serving_mixes_warp_tier_and_block_only_requests(cuda_lib):
         got = [srv.wait(t, capacity=max(r["b"], 1))[0] for t, r in zip(tickets, reqs)]
     for i, (a, b) in enumerate(zip(got, want)):
         assert np.array_equal(a, b), (i, reqs[i]["b"], len(reqs[i]["seeds"]))
+
+
+@pytest.mark.parametrize("class_cap", [0, 1])
+def test_size_classes_take_turns(cuda_lib, class_cap):
+    """Requests on graphs of three size classes (n = 2,000, 2^17 and 2^19: the last with the
+    visited bitmap in global memory) arrive while others run. Each step serves one class, so a
+    request sits out the steps of the other classes; its rounds, random streams and result must
+    still be exactly those of the request run alone. With a per-class cap of one sampled graph per
+    step, each class runs one request at a time and admission passes over a class at its cap."""
+    graphs = [W.tiny_chung_lu_query().graph, W.graph_rmat_wc(17, 1 << 19, seed=41),
+              W.graph_rmat_wc(19, 1 << 20, seed=91)]
+    hs = [cuda_lib.load_graph(g) for g in graphs]
+    rng = np.random.default_rng(43)
+    reqs = []
+    for i in range(9):
+        gi = i % 3
+        g = graphs[gi]
+        reqs.append(dict(driver=int(i % 2), gi=gi, seeds=W.uniform_seeds(g.n, int(rng.integers(5, 40)), 100 + i),
+                         b=int(rng.integers(2, 7)), theta=int(rng.integers(500, 3000)), key=int(rng.integers(1 << 62))))
+    want = [_alone(cuda_lib, hs, r) for r in reqs]
+    with cuda_lib.Server(max_active=8, max_class_samples=class_cap) as srv:
+        tickets = []
+        for i, r in enumerate(reqs):
+            tickets.append(srv.submit(r["driver"], hs[r["gi"]], r["seeds"], r["b"], r["theta"], r["key"]))
+            if i % 3 == 2:
+                time.sleep(0.02)
+        got = [srv.wait(t, capacity=r["b"])[0] for t, r in zip(tickets, reqs)]
+        st = srv.stats()
+    for i, (a, b) in enumerate(zip(got, want)):
+        assert np.array_equal(a, b), (i, reqs[i]["gi"], reqs[i]["driver"])
+    assert st["completed"] == len(reqs) and st["memory_in_use"] == 0
+    r = reqs[1]  # the 2^17 graph: one result against the oracle as well
+    f = O.advanced_greedy if r["driver"] == 0 else O.greedy_replace
+    assert np.array_equal(got[1], f(graphs[1], r["seeds"], r["b"], r["theta"], r["key"]))
