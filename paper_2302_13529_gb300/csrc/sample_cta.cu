@@ -97,7 +97,7 @@ bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint3
         while (2 * slots * 2 <= c->bm_words) slots <<= 1;  // keys + values fit in the bitmap space
     } else {
         c->bm_words = nwords;
-        slots = 2048;  // 16 KB of shared memory for the resolution hash (8 blocks per SM)
+        slots = 2048;  // 16 KB of shared memory for the resolution hash
     }
     c->global_bitmap = smem_bitmap ? 0u : 1u;
     c->tree_words = smem_bitmap ? c->bm_words : 2 * slots;
