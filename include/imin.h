@@ -264,10 +264,10 @@ int imin_autotune_batch(imin_query* queries, int32_t n_queries, int32_t driver, 
 
 /* ---- serving: continuous batching of queries --------------------------------------------
  * A server owns a worker thread and a CUDA stream on the current device. Requests (an
- * AdvancedGreedy or GreedyReplace query on a loaded graph) are admitted in arrival order within
- * their graph-size class whenever a batch slot is free, their device state (about 8n + n/4
- * bytes plus seeds and blockers) fits the memory budget and their class is under its per-step
- * sample cap (more requests of one class per step add little throughput once their samples fill
+ * AdvancedGreedy or GreedyReplace query on a loaded graph) are admitted in arrival order (a
+ * request waiting at its class's cap may be passed by requests that fit, at most 4 of its own
+ * class) whenever a batch slot is free, their device state (about 8n + n/4 bytes plus seeds and
+ * blockers) fits the memory budget and their graph-size class is under its per-step sample cap (more requests of one class per step add little throughput once their samples fill
  * the GPU, and every one of them would finish later). Each step advances the admitted requests of one graph-size
  * class (n <= 2^16, 2^17, 2^18, larger) by one greedy round in shared launches (one Alg. 2 launch
  * over the sampled graphs of those requests, then one selection launch). The class a step
@@ -286,7 +286,8 @@ typedef struct imin_server_config {
     int32_t max_class_samples;  /* sampled graphs per step that one size class may batch across its
                                    requests (0: 200,000). A pending request waits while its class
                                    is at the cap (it runs alone when it exceeds the cap by itself);
-                                   pending requests of other classes are admitted past it. */
+                                   requests of other classes are admitted past it, and so are at
+                                   most 4 later requests of its own class that fit. */
 } imin_server_config;
 
 typedef struct imin_server_stats {

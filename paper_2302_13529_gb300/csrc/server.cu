@@ -35,6 +35,7 @@ using Clock = std::chrono::steady_clock;
 constexpr int kAG = 0;
 constexpr int kGR = 1;
 constexpr int kPrefixRows = kBatchClasses + 1;  // item prefix rows: size classes, warp tier
+constexpr uint32_t kMaxOvertakes = 4;  // later requests of a class that may pass one waiting at the cap
 
 struct Req {
     uint64_t ticket = 0;
@@ -53,6 +54,7 @@ struct Req {
     uint64_t off_seeds = 0, off_excl = 0, off_cb = 0, off_delta = 0, off_blk = 0, off_done = 0;
     bool warp = false;  // its samples go to the warp tier first
     uint32_t cutoff = 0;  // its graph's tuned warp/block cutoff (set at admission)
+    uint32_t overtaken = 0;  // later requests of its class admitted while it waited at the cap
     // result
     bool done = false;
     int status = IMIN_OK;
@@ -268,12 +270,17 @@ void imin_server::run()
                 // fits the budget and the class's samples per step stay under the cap (a class
                 // at its cap is passed over, not waited for)
                 uint64_t class_samples[kBatchClasses] = {};
+                Req* waiting[kBatchClasses] = {};  // the oldest pending request of the class that did not fit
                 for (Req* r : slots)
                     if (r != nullptr) class_samples[batch_class(r->g->n)] += r->theta;
                 for (auto it = pending.begin(); it != pending.end();) {
                     Req* r = *it;
                     const int k = batch_class(r->g->n);
-                    if (class_samples[k] > 0 && class_samples[k] + r->theta > class_cap) {
+                    // later requests of a class that fit under its cap may pass one that does not,
+                    // kMaxOvertakes of them at most; then the class waits for it
+                    const bool held = waiting[k] != nullptr && waiting[k]->overtaken >= kMaxOvertakes;
+                    if (held || (class_samples[k] > 0 && class_samples[k] + r->theta > class_cap)) {
+                        if (waiting[k] == nullptr) waiting[k] = r;
                         ++it;
                         continue;
                     }
@@ -289,6 +296,7 @@ void imin_server::run()
                     slots[free_slot] = r;
                     used += r->bytes;
                     class_samples[k] += r->theta;
+                    if (waiting[k] != nullptr) waiting[k]->overtaken += 1;
                     admitted.push_back(r);
                     st.admitted += 1;
                 }
