@@ -266,6 +266,7 @@ struct Query {
     uint8_t* scratch1 = nullptr;
     uint8_t* scratch2 = nullptr;
     uint8_t* scratch3 = nullptr;
+    uint8_t* handoff = nullptr;  // the warp tier's hand-off snapshots (after the block tier's slots)
     int32_t words = 0;
     explicit Query(cudaStream_t s) : arena(s) {}
 };
@@ -287,7 +288,16 @@ int setup_query(const imin_graph* g, const std::vector<int32_t>& seeds, uint32_t
     IMIN_CUDA(q.arena.alloc(&q.stats, kStCount));
     IMIN_CUDA(q.arena.alloc(&q.scratch1, q.plan.scratch_bytes[1]));
     IMIN_CUDA(q.arena.alloc(&q.scratch2, q.plan.scratch_bytes[2]));
-    IMIN_CUDA(q.arena.alloc(&q.scratch3, q.plan.scratch_bytes[kTierCta]));
+    // with the warp tier in front of the block tier, one hand-off snapshot per sample it may give
+    // up on, after the block tier's slots: the block tier resumes those samples where it stopped
+    uint64_t handoff_bytes = 0;
+    if (q.plan.use_cta && q.plan.cta.from_list && q.plan.blocks[0] > 0) {
+        const Handoff h = handoff_layout(q.plan.cfg[0].rcap, q.plan.cfg[0].dcap, q.plan.cfg[0].ecap);
+        q.plan.cta.handoff_stride = h.stride;
+        handoff_bytes = static_cast<uint64_t>(theta) * h.stride;
+    }
+    IMIN_CUDA(q.arena.alloc(&q.scratch3, q.plan.scratch_bytes[kTierCta] + handoff_bytes));
+    if (handoff_bytes > 0) q.handoff = q.scratch3 + q.plan.scratch_bytes[kTierCta];
     if (q.plan.use_cta) IMIN_CUDA(prepare_cta_scratch(q.plan.cta, q.plan.blocks[kTierCta], q.scratch3, s));
     IMIN_CUDA(cudaMemcpyAsync(q.seeds, seeds.data(), sizeof(int32_t) * seeds.size(),
                               cudaMemcpyHostToDevice, s));
@@ -311,7 +321,7 @@ cudaError_t enqueue_call(const SampleParams& P, const Query& q, CallTimer& T)
     const int count = 3;
     for (int k = 0; k < count; ++k) {
         const int t = order[k];
-        uint8_t* scr = t == 1 ? q.scratch1 : (t == 2 ? q.scratch2 : (t == kTierCta ? q.scratch3 : nullptr));
+        uint8_t* scr = t == 1 ? q.scratch1 : (t == 2 ? q.scratch2 : (t == kTierCta ? q.scratch3 : q.handoff));
         const int kind = t == kTierCta ? kKindCta : kKindTier0 + t;
         const cudaError_t e = T.run(kind, [&](bool* launched) {
             return launch_sample_tier(t, P, q.plan, scr, T.s, launched);

@@ -181,6 +181,24 @@ struct TierCfg {
     uint32_t next_tier;     // tier that re-runs this tier's overflowing samples
 };
 
+// Hand-off snapshot of a sample the warp tier 0 gave up on, taken at the start of the BFS level
+// it could not hold: header words (sample, lb, le, nlev, nE, offsets of gid, par and edges), the
+// level offsets lvl[0..nlev], gid[0..le), par[0..le) and the non-tree edges recorded before that
+// level, as (local source, global target). The block tier resumes the sample from it instead of
+// running the first levels again. Sizes follow the warp tier's capacities (rcap, dcap, ecap).
+struct Handoff {
+    uint32_t off_gid, off_par, off_edges, stride;
+};
+__host__ __device__ inline Handoff handoff_layout(uint32_t rcap, uint32_t dcap, uint32_t ecap)
+{
+    Handoff h;
+    h.off_gid = (32u + 4u * (dcap + 1u) + 15u) & ~15u;
+    h.off_par = h.off_gid + ((4u * rcap + 15u) & ~15u);
+    h.off_edges = h.off_par + ((4u * rcap + 15u) & ~15u);
+    h.stride = h.off_edges + ((8u * ecap + 15u) & ~15u);
+    return h;
+}
+
 // Block-per-sample tier (sample_cta.cu): per-block slot layout and shared-memory sizes.
 struct CtaCfg {
     uint32_t bm_words;    // visited bitmap words (>= n/32)
@@ -191,6 +209,8 @@ struct CtaCfg {
     uint32_t global_bitmap;  // 1: the bitmap is in the slot (large n); 0: in shared memory,
                              // where it also holds the resolution hash
     uint32_t tree_words;     // shared words free after the BFS for the packed tree (one per vertex)
+    uint32_t handoff_stride; // 0: none; else the bytes of one warp-tier hand-off snapshot, stored
+                             // by list position after the grid's slots (Handoff below)
     uint64_t off_bm, off_gid, off_par, off_idom, off_rows, off_edges, slot_bytes;
     uint8_t* scratch;
     uint32_t from_list;   // 1: take the samples that tier 0 handed over; 0: all of [0, theta)
@@ -347,7 +367,8 @@ enum SampleResult { kSampleDone = 0, kSampleOverflow = 1, kSampleError = 2 };
 // (small shared tables) instead of the slots recorded in hslot[].
 template <bool G, bool kClearAll, int M = kModelAny>
 __device__ __forceinline__ int run_sample(const SampleParams& P, const WarpSpace<G>& w,
-                                          uint32_t j, uint32_t lane, SampleCounters& sc)
+                                          uint32_t j, uint32_t lane, SampleCounters& sc,
+                                          uint32_t* level_state = nullptr)
 {
     const uint32_t ns = P.ns;
     const uint32_t hmask = w.hcap - 1;
@@ -372,7 +393,9 @@ __device__ __forceinline__ int run_sample(const SampleParams& P, const WarpSpace
     unsigned long long examined = 0, live = 0;
 
     uint32_t lb = 1, le = 1 + ns;
+    uint32_t nE_level = 0;  // non-tree edges recorded before the current level
     while (lb < le) {
+        nE_level = nE;
         for (uint32_t base = lb; base < le && !over; base += 32) {
             // ---- the frontier vertices of this chunk and their edge groups
             const uint32_t idx = base + lane;
@@ -508,6 +531,12 @@ __device__ __forceinline__ int run_sample(const SampleParams& P, const WarpSpace
     }
 
     if (over) {
+        if (level_state != nullptr) {  // where a hand-off would resume: the start of this level
+            level_state[0] = lb;
+            level_state[1] = le;
+            level_state[2] = nlev;
+            level_state[3] = nE_level;
+        }
         // abandon: clear every hash slot this sample used
         if constexpr (kClearAll) {
             for (uint32_t i = lane; i < w.hcap; i += 32) w.hkey[i] = kEmpty;

@@ -50,7 +50,18 @@ __global__ void __launch_bounds__(cta_threads<kSmemBitmap>(), 1024 / cta_threads
             C.from_list ? *reinterpret_cast<const volatile uint32_t*>(&P.ctl->count[kTierCta]) : P.theta;
         if (sh.item >= total) break;
         const uint32_t j = C.from_list ? P.lists[kTierCta * P.theta + sh.item] : sh.item;
-        const int rc = run_sample_cta<kSmemBitmap, false, M>(P, C, bm, dsm, sh, S, j, tid, sc, examined, live);
+        int rc;
+        if (C.handoff_stride != 0) {
+            // the warp tier left this sample's state at the level it could not hold: resume there
+            const uint8_t* hb = C.scratch + static_cast<uint64_t>(gridDim.x) * C.slot_bytes +
+                                static_cast<uint64_t>(sh.item) * C.handoff_stride;
+            uint32_t from[3];
+            restore_handoff<kCtaThreads>(P, hb, S, bm, sh, tid, from);
+            rc = run_sample_cta<kSmemBitmap, false, M>(P, C, bm, dsm, sh, S, j, tid, sc, examined, live,
+                                                       ExtraBlocked{nullptr, 0u}, from);
+        } else {
+            rc = run_sample_cta<kSmemBitmap, false, M>(P, C, bm, dsm, sh, S, j, tid, sc, examined, live);
+        }
         if (tid == 0) {
             if (rc == kSampleOverflow) {
                 const uint32_t pos = atomicAdd(&P.ctl->count[kTierWhole], 1u);
@@ -100,6 +111,7 @@ bool plan_cta_tier(const DeviceInfo& dev, int32_t n, int32_t m, CtaCfg* c, uint3
         slots = 2048;  // 16 KB of shared memory for the resolution hash
     }
     c->global_bitmap = smem_bitmap ? 0u : 1u;
+    c->handoff_stride = 0;  // set per query when the warp tier runs in front (api.cu)
     c->tree_words = smem_bitmap ? c->bm_words : 2 * slots;
     c->res_slots = slots;
     uint32_t bits = 0;

@@ -389,40 +389,92 @@ __device__ __forceinline__ void tree_sweep_packed(const SampleParams& P, CtaShar
     __syncthreads();
 }
 
+// Restores a warp-tier hand-off snapshot (Handoff, at hb) into the block's slot and visited
+// bitmap and into sh, and sets from = (lb, le, nlev) for run_sample_cta: the sample continues
+// at the start of the level the warp tier could not hold, with the ids, parents, level offsets
+// and non-tree edges the warp tier had found before it. Ids are in the warp tier's discovery
+// order, which is a BFS order like the block tier's own.
+template <uint32_t T>
+__device__ __forceinline__ void restore_handoff(const SampleParams& P, const uint8_t* hb, const Slot& S,
+                                                uint32_t* bm, CtaShared<T>& sh, uint32_t tid, uint32_t from[3])
+{
+    const uint32_t* hdr = reinterpret_cast<const uint32_t*>(hb);
+    const uint32_t lb = hdr[1], le = hdr[2], nlev = min(hdr[3], kCtaLevels), ne = hdr[4];
+    const int32_t* hg = reinterpret_cast<const int32_t*>(hb + hdr[5]);
+    const uint32_t* hp = reinterpret_cast<const uint32_t*>(hb + hdr[6]);
+    const uint2* he = reinterpret_cast<const uint2*>(hb + hdr[7]);
+    const uint32_t ns = P.ns;
+    for (uint32_t i = tid; i < le; i += T) {
+        if (i == 0) {
+            S.par[0] = 0;
+            S.idom[0] = 0;
+            continue;
+        }
+        const int32_t v = hg[i];
+        const uint32_t p = hp[i];
+        S.gid[i] = v;
+        S.par[i] = p;
+        S.idom[i] = p;
+        if (i >= lb) S.rows[i] = make_int2(__ldg(P.g.row_ptr + v), __ldg(P.g.row_ptr + v + 1));
+        if (i >= 1 + ns) atomicOr(bm + (static_cast<uint32_t>(v) >> 5), 1u << (v & 31));
+    }
+    for (uint32_t k = tid; k < ne; k += T) S.edges[k] = he[k];
+    for (uint32_t i = tid; i <= nlev; i += T) sh.lvl[i] = hdr[8 + i];
+    if (tid == 0) {
+        sh.nR = le;
+        sh.nE = ne;
+        sh.flag = 0;
+    }
+    from[0] = lb;
+    from[1] = le;
+    from[2] = nlev;
+    __syncthreads();
+}
+
 // bm: visited bitmap (shared or global memory); res: 2 * C.res_slots words of shared memory for
 // the non-tree target resolution -- the bitmap itself when kResInBitmap (it is cleared first).
 // kSpread: only the BFS; |R| (seeds included) is added to sc.reached and the dominator step is
 // skipped (the Monte-Carlo spread estimate of Def. 3); xb lists vertices blocked in this sample
-// only (reachability mode).
+// only (reachability mode). `from` (lb, le, nlev) resumes a sample at the start of a level whose
+// state the caller restored (restore_handoff).
 template <bool kResInBitmap, bool kSpread = false, int M = kModelAny, uint32_t T>
 __device__ __forceinline__ int run_sample_cta(const SampleParams& P, const CtaCfg& C, uint32_t* bm,
                                               uint32_t* res, CtaShared<T>& sh, const Slot& S, uint32_t j,
                                               uint32_t tid, SampleCounters& sc,
                                               unsigned long long& examined, unsigned long long& live,
-                                              ExtraBlocked xb = ExtraBlocked{nullptr, 0u})
+                                              ExtraBlocked xb = ExtraBlocked{nullptr, 0u},
+                                              const uint32_t* from = nullptr)
 {
     constexpr uint32_t kCtaThreads = T, kCtaWarps = CtaDims<T>::kWarps, kChunk = CtaDims<T>::kChunk;
     const uint32_t ns = P.ns;
     const uint32_t lane = tid & 31, wid = tid >> 5;
-    for (uint32_t i = tid; i < ns; i += kCtaThreads) {
-        const int32_t u = P.seeds[i];
-        S.gid[1 + i] = u;
-        S.idom[1 + i] = 0;
-        S.par[1 + i] = 0;
-        S.rows[1 + i] = make_int2(__ldg(P.g.row_ptr + u), __ldg(P.g.row_ptr + u + 1));
-    }
-    if (tid == 0) {
-        S.idom[0] = 0;
-        S.par[0] = 0;
-        sh.lvl[0] = 1;
-        sh.lvl[1] = 1 + ns;
-        sh.nR = 1 + ns;
-        sh.nE = 0;
-        sh.flag = 0;
-    }
-    __syncthreads();
-
     uint32_t lb = 1, le = 1 + ns, nlev = 1;
+    if (from == nullptr) {
+        for (uint32_t i = tid; i < ns; i += kCtaThreads) {
+            const int32_t u = P.seeds[i];
+            S.gid[1 + i] = u;
+            S.idom[1 + i] = 0;
+            S.par[1 + i] = 0;
+            S.rows[1 + i] = make_int2(__ldg(P.g.row_ptr + u), __ldg(P.g.row_ptr + u + 1));
+        }
+        if (tid == 0) {
+            S.idom[0] = 0;
+            S.par[0] = 0;
+            sh.lvl[0] = 1;
+            sh.lvl[1] = 1 + ns;
+            sh.nR = 1 + ns;
+            sh.nE = 0;
+            sh.flag = 0;
+        }
+        __syncthreads();
+    } else {
+        // resumed at the start of a level: the caller restored the slot arrays of ids below le,
+        // the rows of the level's vertices, the visited bits, sh.lvl, sh.nR and sh.nE
+        lb = from[0];
+        le = from[1];
+        nlev = from[2];
+    }
+
     unsigned long long ex = 0, lv = 0;
     bool over = false;
     while (lb < le) {
