@@ -1079,7 +1079,23 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream, uint32_t 
         IMIN_CUDA(prepare_cta_scratch(cfg[kBatchGlobalClass], cta_blocks[kBatchGlobalClass], global_scratch, s));
     IMIN_CUDA(arena.alloc(&whole_scratch, wp.scratch_bytes[kTierWhole]));
     IMIN_CUDA(arena.alloc(&stats, kStCount));
-    IMIN_CUDA(arena.alloc(&over, sum_theta));
+    // hand-off snapshots of the samples the warp tier gives up on, per size class after the
+    // overflow items (at most 1 GiB in all; samples beyond the lists' room run from the start)
+    const uint32_t over_cap = static_cast<uint32_t>(std::min<uint64_t>(sum_theta, 0xFFFFFFFFull));
+    uint32_t handoff_stride = 0, handoff_cap = 0;
+    uint64_t warp_theta = 0;
+    for (int32_t i = 0; i < nq; ++i)
+        if (warp_q[i]) warp_theta += qs[i].theta;
+    if (warp_theta > 0) {
+        const Handoff h = handoff_layout(wcfg.rcap, wcfg.dcap, wcfg.ecap);
+        handoff_stride = h.stride;
+        handoff_cap = static_cast<uint32_t>(
+            std::min<uint64_t>(warp_theta, (1ull << 30) / (static_cast<uint64_t>(kBatchClasses) * h.stride)));
+    }
+    uint8_t* over_raw = nullptr;
+    IMIN_CUDA(arena.alloc(&over_raw, batch_handoff_offset(over_cap) +
+                                         static_cast<uint64_t>(kBatchClasses) * handoff_cap * handoff_stride));
+    over = reinterpret_cast<uint2*>(over_raw);
     IMIN_CUDA(arena.alloc(&cb_counts, nq));
     IMIN_CUDA(cudaMemsetAsync(buf, 0, total, s));
     IMIN_CUDA(cudaMemsetAsync(whole_scratch, 0xFF, wp.scratch_bytes[kTierWhole], s));
@@ -1188,7 +1204,9 @@ int batch_impl(Driver which, imin_query* qs, int32_t nq, void* stream, uint32_t 
         B.step = static_cast<uint32_t>(c);
         B.ctl = ctl + c;
         B.over = over;
-        B.over_cap = static_cast<uint32_t>(std::min<uint64_t>(sum_theta, 0xFFFFFFFFull));
+        B.over_cap = over_cap;
+        B.handoff_stride = handoff_stride;
+        B.handoff_cap = handoff_cap;
         B.stats = stats;
         B.all_ic = all_ic ? 1u : 0u;
         if (gr) {  // phase-2 unblocking of every GreedyReplace query at this step

@@ -127,13 +127,44 @@ __global__ void __launch_bounds__(cta_threads<kSmemBitmap>(), 1024 / cta_threads
         const unsigned long long j0 = (item - B.prefix[q]) * B.chunk;
         const unsigned long long j1 = min(j0 + B.chunk, static_cast<unsigned long long>(Q.theta));
         for (unsigned long long j = j0; j < j1; ++j) {
-            if (Q.done != nullptr && Q.done[j] != 0) continue;  // the warp tier finished it
+            if (Q.done != nullptr && Q.done[j] != 0) continue;  // finished or handed over by the warp tier
             const int rc = run_sample_cta<kSmemBitmap, false, M>(P, C, bm, dsm, sh, S, static_cast<uint32_t>(j), tid,
                                                        sc, examined, live);
             if (tid == 0) {
                 if (rc == kSampleOverflow) {
                     const uint32_t p = atomicAdd(&B.ctl->over_count, 1u);
                     if (p < B.over_cap) B.over[p] = make_uint2(q, static_cast<uint32_t>(j));
+                    else atomicOr(&B.ctl->error, kErrCapacity);
+                } else if (rc == kSampleError) {
+                    atomicOr(&B.ctl->error, kErrInternal);
+                }
+            }
+        }
+    }
+    // the samples of this class the warp tier handed over: resume each at the level it stopped
+    if (B.handoff_stride != 0) {
+        const uint32_t count =
+            min(*reinterpret_cast<const volatile uint32_t*>(&B.ctl->handoff_count[B.cls]), B.handoff_cap);
+        const uint8_t* list = reinterpret_cast<const uint8_t*>(B.over) + batch_handoff_offset(B.over_cap) +
+                              static_cast<uint64_t>(B.cls) * B.handoff_cap * B.handoff_stride;
+        for (;;) {
+            __syncthreads();
+            if (tid == 0) s_item = atomicAdd(&B.ctl->handoff_cursor[B.cls], 1u);
+            __syncthreads();
+            const unsigned long long h = s_item;
+            if (h >= count) break;
+            const uint8_t* hb = list + h * B.handoff_stride;
+            const uint32_t* hdr = reinterpret_cast<const uint32_t*>(hb);
+            const uint32_t j = hdr[0], q = hdr[8];
+            const SampleParams P = params_of(B.q[q], B.step - B.q[q].start);
+            uint32_t from[3];
+            restore_handoff<kCtaThreads>(P, hb, S, bm, sh, tid, from);
+            const int rc = run_sample_cta<kSmemBitmap, false, M>(P, C, bm, dsm, sh, S, j, tid, sc, examined, live,
+                                                                 ExtraBlocked{nullptr, 0u}, from);
+            if (tid == 0) {
+                if (rc == kSampleOverflow) {
+                    const uint32_t p = atomicAdd(&B.ctl->over_count, 1u);
+                    if (p < B.over_cap) B.over[p] = make_uint2(q, j);
                     else atomicOr(&B.ctl->error, kErrCapacity);
                 } else if (rc == kSampleError) {
                     atomicOr(&B.ctl->error, kErrInternal);
@@ -165,7 +196,9 @@ __global__ void __launch_bounds__(cta_threads<kSmemBitmap>(), 1024 / cta_threads
 
 // The warp tier of a step: one warp per sample, working set in shared memory with the
 // warp/block cutoff as capacity, over the active queries that have a `done` array. Each
-// sample's outcome is stored in done[j] (1: counted here; 0: left to the block tier).
+// sample's outcome is stored in done[j]: 1, counted here; 2, given up on and left as a hand-off
+// snapshot in its size class's list (B.handoff_stride != 0, while the list has room), which the
+// class's block launch resumes; 0, left to the block tier to run from the start.
 template <int M>
 __global__ void __launch_bounds__(kBatchWarps * 32, 4) k_batch_warp(BatchStep B, TierCfg T)
 {
@@ -208,9 +241,24 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4) k_batch_warp(BatchStep B,
         const unsigned long long j0 = (item - B.prefix[q]) * B.chunk;
         const unsigned long long j1 = min(j0 + B.chunk, static_cast<unsigned long long>(Q.theta));
         for (unsigned long long j = j0; j < j1; ++j) {
-            const int rc = run_sample<false, true, M>(P, w, static_cast<uint32_t>(j), lane, sc);
+            uint32_t at[4];
+            const int rc = run_sample<false, true, M>(P, w, static_cast<uint32_t>(j), lane, sc, at);
+            uint8_t outcome = rc == kSampleDone ? 1 : 0;
+            if (rc == kSampleOverflow && B.handoff_stride != 0) {
+                const uint32_t k = static_cast<uint32_t>(batch_class(Q.g.n));
+                uint32_t pos = 0;
+                if (lane == 0) pos = atomicAdd(&B.ctl->handoff_count[k], 1u);
+                pos = __shfl_sync(kFull, pos, 0);
+                if (pos < B.handoff_cap) {
+                    const Handoff h = handoff_layout(T.rcap, T.dcap, T.ecap);
+                    uint8_t* hb = reinterpret_cast<uint8_t*>(B.over) + batch_handoff_offset(B.over_cap) +
+                                  (static_cast<uint64_t>(k) * B.handoff_cap + pos) * B.handoff_stride;
+                    write_handoff(w, lane, hb, h, static_cast<uint32_t>(j), q, at);
+                    outcome = 2;
+                }
+            }
             if (lane == 0) {
-                Q.done[j] = rc == kSampleDone ? 1 : 0;
+                Q.done[j] = outcome;
                 if (rc == kSampleError) atomicOr(&B.ctl->error, kErrInternal);
             }
         }

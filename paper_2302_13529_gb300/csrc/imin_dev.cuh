@@ -182,17 +182,19 @@ struct TierCfg {
 };
 
 // Hand-off snapshot of a sample the warp tier 0 gave up on, taken at the start of the BFS level
-// it could not hold: header words (sample, lb, le, nlev, nE, offsets of gid, par and edges), the
-// level offsets lvl[0..nlev], gid[0..le), par[0..le) and the non-tree edges recorded before that
-// level, as (local source, global target). The block tier resumes the sample from it instead of
-// running the first levels again. Sizes follow the warp tier's capacities (rcap, dcap, ecap).
+// it could not hold: kHandoffHeader header words (sample, lb, le, nlev, nE, offsets of gid, par
+// and edges, query of a batch), the level offsets lvl[0..nlev], gid[0..le), par[0..le) and the
+// non-tree edges recorded before that level, as (local source, global target). The block tier
+// resumes the sample from it instead of running the first levels again. Sizes follow the warp
+// tier's capacities (rcap, dcap, ecap).
+constexpr uint32_t kHandoffHeader = 16;
 struct Handoff {
     uint32_t off_gid, off_par, off_edges, stride;
 };
 __host__ __device__ inline Handoff handoff_layout(uint32_t rcap, uint32_t dcap, uint32_t ecap)
 {
     Handoff h;
-    h.off_gid = (32u + 4u * (dcap + 1u) + 15u) & ~15u;
+    h.off_gid = (4u * (kHandoffHeader + dcap + 1u) + 15u) & ~15u;
     h.off_par = h.off_gid + ((4u * rcap + 15u) & ~15u);
     h.off_edges = h.off_par + ((4u * rcap + 15u) & ~15u);
     h.stride = h.off_edges + ((8u * ecap + 15u) & ~15u);
@@ -253,6 +255,8 @@ struct BatchCtl {
     uint32_t error;
     uint32_t pad;
     unsigned long long warp_cursor;  // next (query, sample chunk) item of the warp tier
+    uint32_t handoff_count[kBatchClasses];   // hand-off snapshots the warp tier left per class
+    uint32_t handoff_cursor[kBatchClasses];  // next snapshot the class's block launch resumes
 };
 
 // One greedy step of a batch: round `step` of every query that is still active.
@@ -264,12 +268,21 @@ struct BatchStep {
     uint32_t chunk;                    // samples per item
     uint32_t cls;                      // size class of this launch
     uint32_t step;
+    uint32_t handoff_stride;           // 0: no hand-off; else the bytes of one snapshot (Handoff)
     BatchCtl* ctl;
-    uint2* over;                       // (query, sample) overflow items
+    uint2* over;                       // (query, sample) overflow items, then (handoff_stride != 0)
+                                       // handoff_cap snapshots per size class (batch_handoff_base)
     uint32_t over_cap;
+    uint32_t handoff_cap;              // hand-off snapshots per size class
     unsigned long long* stats;
     uint32_t all_ic;                   // 1: every query's graph uses the IC model
 };
+
+// The hand-off snapshots of size class k in a batched step: after the overflow items.
+__host__ __device__ inline uint64_t batch_handoff_offset(uint32_t over_cap)
+{
+    return (8ull * over_cap + 255) & ~255ull;
+}
 
 // Byte layout of one warp's working set (same for shared and global memory).
 struct WarpLayout {
@@ -610,5 +623,42 @@ __device__ __forceinline__ int run_sample(const SampleParams& P, const WarpSpace
     sc.done += 1;
     return broken ? kSampleError : kSampleDone;
 }
+
+// Writes the hand-off snapshot (Handoff, at hb) of the sample in warp space w that run_sample
+// just gave up on, from the level state it reported (at: lb, le, nlev, nE at the start of the
+// level it could not hold); q is the sample's query in a batch (0 otherwise). The warp's arrays
+// still hold the sample: the abandon only cleared its hash keys.
+template <bool G>
+__device__ __forceinline__ void write_handoff(const WarpSpace<G>& w, uint32_t lane, uint8_t* hb, const Handoff& h,
+                                              uint32_t j, uint32_t q, const uint32_t at[4])
+{
+    uint32_t* hdr = reinterpret_cast<uint32_t*>(hb);
+    const uint32_t le = at[1], nlev = at[2], ne = at[3];
+    if (lane == 0) {
+        hdr[0] = j;
+        hdr[1] = at[0];
+        hdr[2] = le;
+        hdr[3] = nlev;
+        hdr[4] = ne;
+        hdr[5] = h.off_gid;
+        hdr[6] = h.off_par;
+        hdr[7] = h.off_edges;
+        hdr[8] = q;
+    }
+    for (uint32_t i = lane; i <= nlev; i += 32) hdr[kHandoffHeader + i] = w.lvl[i];
+    int32_t* hg = reinterpret_cast<int32_t*>(hb + h.off_gid);
+    uint32_t* hp = reinterpret_cast<uint32_t*>(hb + h.off_par);
+    for (uint32_t i = lane; i < le; i += 32) {
+        hg[i] = w.gid[i];
+        hp[i] = w.par[i];
+    }
+    uint2* he = reinterpret_cast<uint2*>(hb + h.off_edges);
+    for (uint32_t k = lane; k < ne; k += 32) {
+        const uint2 e = w.edges[k];
+        he[k] = make_uint2(e.x, static_cast<uint32_t>(w.gid[e.y]));
+    }
+    __syncwarp();
+}
+
 
 }  // namespace imin

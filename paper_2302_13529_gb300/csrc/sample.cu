@@ -109,32 +109,7 @@ k_sample_tier(SampleParams P, TierCfg T)
                 if (T.gscratch != nullptr) {
                     pos = __shfl_sync(kFull, pos, 0);
                     const Handoff h = handoff_layout(T.rcap, T.dcap, T.ecap);
-                    uint8_t* hb = T.gscratch + static_cast<uint64_t>(pos) * h.stride;
-                    uint32_t* hdr = reinterpret_cast<uint32_t*>(hb);
-                    const uint32_t le = at[1], nlev = at[2], ne = at[3];
-                    if (lane == 0) {
-                        hdr[0] = j;
-                        hdr[1] = at[0];
-                        hdr[2] = le;
-                        hdr[3] = nlev;
-                        hdr[4] = ne;
-                        hdr[5] = h.off_gid;
-                        hdr[6] = h.off_par;
-                        hdr[7] = h.off_edges;
-                    }
-                    for (uint32_t i = lane; i <= nlev; i += 32) hdr[8 + i] = w.lvl[i];
-                    int32_t* hg = reinterpret_cast<int32_t*>(hb + h.off_gid);
-                    uint32_t* hp = reinterpret_cast<uint32_t*>(hb + h.off_par);
-                    for (uint32_t i = lane; i < le; i += 32) {
-                        hg[i] = w.gid[i];
-                        hp[i] = w.par[i];
-                    }
-                    uint2* he = reinterpret_cast<uint2*>(hb + h.off_edges);
-                    for (uint32_t k = lane; k < ne; k += 32) {
-                        const uint2 e = w.edges[k];
-                        he[k] = make_uint2(e.x, static_cast<uint32_t>(w.gid[e.y]));
-                    }
-                    __syncwarp();
+                    write_handoff(w, lane, T.gscratch + static_cast<uint64_t>(pos) * h.stride, h, j, 0u, at);
                 }
             }
         } else if (rc == kSampleError) {

@@ -419,7 +419,7 @@ __device__ __forceinline__ void restore_handoff(const SampleParams& P, const uin
         if (i >= 1 + ns) atomicOr(bm + (static_cast<uint32_t>(v) >> 5), 1u << (v & 31));
     }
     for (uint32_t k = tid; k < ne; k += T) S.edges[k] = he[k];
-    for (uint32_t i = tid; i <= nlev; i += T) sh.lvl[i] = hdr[8 + i];
+    for (uint32_t i = tid; i <= nlev; i += T) sh.lvl[i] = hdr[kHandoffHeader + i];
     if (tid == 0) {
         sh.nR = le;
         sh.nE = ne;
