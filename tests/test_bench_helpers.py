@@ -82,6 +82,21 @@ def test_ncu_figures_follow_the_source_hash(tmp_path, monkeypatch):
     assert r["bound"] == "hbm" and r["traffic"] is None and "ncu" not in r
 
 
+def test_committed_profiles_match_the_kernel_sources():
+    """Every committed ncu summary that names a source hash was taken on the current kernel
+    sources: a kernel change without a new capture would leave counters that describe other
+    code (and bench.py would drop their traffic figure)."""
+    prof_dir = os.path.join(bench.ROOT, "profiles")
+    current = bench.kernel_source_hash()
+    checked = 0
+    for name in sorted(os.listdir(prof_dir)):
+        for line in open(os.path.join(prof_dir, name)):
+            if line.startswith("source_hash:"):
+                assert line.split(":", 1)[1].strip() == current, name
+                checked += 1
+    assert checked >= 3
+
+
 def test_committed_profile_names_its_kernel_sources():
     """The committed block-tier summary carries a source hash and a traffic figure."""
     path = os.path.join(bench.ROOT, "profiles", f"k_sample_cta_{bench.WORKLOAD}.md")
